@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Throughput of NSG search on one GB300: queries/s at recall@10 >= 0.95.
+
+Workload: the SIFT-shaped synthetic set (1,000,000 x 128 integer values 0..255
+from a 100-component Gaussian mixture, 10,000 queries), index built with the
+paper's Alg. 2 at K=100, L=40, R=50, C=500.  The pool size L is swept over
+100, 125, ..., 400 (k=100); the reported point is the highest-QPS L whose
+mean recall@10 (Eq. 1, against the exact ground truth) is >= 0.95.
+
+A step = one nsg_search_ex launch over the whole 10,000-query batch, inputs
+resident in HBM.  The base (512 MB) is larger than L2 (129 MB).
+`e2e` repeats the step through the public API with pinned host buffers:
+host->device copy of the queries, search, device->host copy of the ids.
+
+Multi-GPU: queries are independent, so each rank searches its own batch on
+its own replica of the index (weak scaling, no collective on the data path).
+
+--impl reference times the CPU oracle (serial scan, exact: recall 1.0) on a
+bounded query sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "queries/sec at recall@10=0.95 on 1 GB300, chosen vs plain form; % HBM peak"
+UNIT = "queries/s"
+BUILD = dict(K=100, L=40, R=50, C=500)
+L_GRID = list(range(100, 401, 25))
+K_RESULTS = 100
+TARGET = 0.95
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="sift")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.rows, self.proc = [], None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9
+                          for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("common.cuh", "search_core.cuh", "search.cu"):
+        with open(os.path.join(ROOT, "paper_1707_00143_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ncu DRAM traffic of the search kernel per query on this workload, keyed by
+# the hash of the kernel sources it was measured on (see profiles/).  A source
+# change invalidates it and `traffic` becomes null until re-measured.
+NCU_TRAFFIC = {}
+
+
+def cpu_serial_scan(base, q, budget_s=10.0):
+    """Oracle serial scan (exact kNN: recall 1.0) on a bounded query sample."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    oracle.knn_query(base, q[:16], 10, nthreads=cores)
+    per_q = (time.perf_counter() - t) / 16
+    m = int(max(16, min(len(q), budget_s / max(per_q, 1e-6))))
+    t = time.perf_counter()
+    oracle.knn_query(base, q[:m], 10, nthreads=cores)
+    el = time.perf_counter() - t
+    return {"value": m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"serial scan (exact kNN, recall@10 = 1.0) of the first {m} queries against "
+                      f"the full {len(base)}-row base, {cores} host threads"}
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_1707_00143_gb300 import datagen
+    import oracle
+
+    oracle.compile_lib()
+    base, q = datagen.workload(args.workload)
+    cores = os.cpu_count() or 1
+    m = 64
+    times = []
+    for s in range(args.warmup + args.steps):
+        qs = q[(s * m) % len(q):(s * m) % len(q) + m]
+        t = time.perf_counter()
+        oracle.knn_query(base, qs, 10, nthreads=cores)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t)
+    ms = 1e3 * sum(times) / len(times)
+    v = m / (ms / 1e3)
+    sample = (f"serial scan (exact kNN, recall@10 = 1.0) of {m} queries per step against the full "
+              f"{len(base)}-row base, {cores} host threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: 1,000,000 x 128 int 0..255, serial scan", "k": 10},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_1707_00143_gb300 import build as nsg_build_mod
+    from paper_1707_00143_gb300 import capi, datagen
+
+    if rank == 0:
+        nsg_build_mod.build()
+    if world > 1:
+        dist.barrier()
+    capi.lib()
+
+    # inputs: same base on every rank (a replica), a distinct query batch per rank
+    base, q = datagen.workload(args.workload, seed_query=datagen.SEED_QUERY + 1000 * rank)
+    n, d = base.shape
+    nq = len(q)
+    bt = torch.from_numpy(base).cuda()
+    qt = torch.from_numpy(q).cuda()
+    st = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    idx = capi.nsg_build(bt, BUILD["K"], BUILD["L"], BUILD["R"], BUILD["C"], seed=0)
+    build_s = time.perf_counter() - t0
+    info = idx.info()
+    gt, _ = capi.nsg_knn_query(bt, qt, 10)
+
+    # sweep L: recall@10 and a quick timing per point
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = None
+    sweep = []
+    for L in L_GRID:
+        out = idx.search_ex(qt, K_RESULTS, L, out=out, counters=False)
+        hits = capi.nsg_recall(out["ids"][:, :10].contiguous(), gt, 10)
+        rec = hits.sum().item() / (10.0 * nq)
+        ev0.record(st)
+        for _ in range(2):
+            idx.search_ex(qt, K_RESULTS, L, out=out, counters=False)
+        ev1.record(st)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1) / 2
+        sweep.append({"L": L, "recall10": rec, "qps": nq / (ms / 1e3)})
+    ok = [s for s in sweep if s["recall10"] >= TARGET]
+    chosen = max(ok, key=lambda s: s["qps"]) if ok else max(sweep, key=lambda s: s["recall10"])
+    L = chosen["L"]
+
+    # algorithmic bytes at the chosen L: unique distance and expansion counts
+    big = capi.SearchParams(0, 16384, capi.PREC_F32, 0)
+    cnt = idx.search_ex(qt, K_RESULTS, L, params=big)
+    n_dist = cnt["n_dist"].to(torch.int64).sum().item()
+    n_expand = cnt["n_expand"].to(torch.int64).sum().item()
+    R = info["R"]
+    bytes_launch = n_dist * d * 4 + n_expand * (R * 4) + nq * (d * 4 + K_RESULTS * 8)
+
+    # timed region: inputs resident in HBM, one search launch per step
+    for _ in range(args.warmup):
+        idx.search_ex(qt, K_RESULTS, L, out=out, counters=False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = ClockSampler(local)
+    time.sleep(0.4)
+    torch.cuda.synchronize()
+    ev0.record(st)
+    for _ in range(args.steps):
+        idx.search_ex(qt, K_RESULTS, L, out=out, counters=False)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms_step = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = t.item()
+        dist.barrier()
+    final_hits = capi.nsg_recall(out["ids"][:, :10].contiguous(), gt, 10)
+    recall10 = final_hits.sum().item() / (10.0 * nq)
+
+    # end to end through the public API with pinned host buffers
+    qh = torch.from_numpy(q).pin_memory()
+    ids_h = torch.empty((nq, K_RESULTS), dtype=torch.int32).pin_memory()
+    qd = torch.empty_like(qt)
+    for i in range(args.warmup + args.steps):
+        if i == args.warmup:
+            torch.cuda.synchronize()
+            e2e_t0 = time.perf_counter()
+        qd.copy_(qh, non_blocking=True)
+        o = idx.search_ex(qd, K_RESULTS, L, out=out, counters=False)
+        ids_h.copy_(o["ids"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_ms = 1e3 * (time.perf_counter() - e2e_t0) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = t.item()
+
+    peak, peak_kind = peaks()
+    achieved = bytes_launch / (ms_step / 1e3) / 1e9
+    src = kernel_source_hash()
+    tr = NCU_TRAFFIC.get(src)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": (tr * nq if tr else None),
+                "peak_kind": peak_kind, "kernel": "search_kernel", "algorithmic_bytes": bytes_launch,
+                "kernel_src": src}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_serial_scan(base, q)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * nq / (ms_step / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "sift-shaped 1,000,000 x 128 int 0..255 GMM(100), 10,000 queries",
+                       "form": "plain", "build": BUILD, "k": K_RESULTS, "L": L,
+                       "recall10": recall10, "target_recall10": TARGET, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (512 MB base)"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * nq / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": nq * d * 4, "d2h_bytes_per_step": nq * K_RESULTS * 4},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "build_seconds": build_s,
+            "build_ms": {k: info[k] for k in ("ms_knn", "ms_centroid_nav", "ms_collect", "ms_prune",
+                                               "ms_connect", "ms_total")},
+            "index": {"avg_degree": info["avg_degree"], "max_degree": info["max_degree"],
+                      "fixup_edges": info["n_fixup_edges"], "nav": info["nav"]},
+            "per_query": {"n_expand": n_expand / nq, "n_dist": n_dist / nq},
+            "sweep": sweep,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * nsg.h -- C ABI of the GB300 (sm_103a) hot path of the Navigating
+ * Spreading-out Graph (NSG; Fu, Xiang, Wang, Cai).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Distances are SQUARED l2 (Section 2 defines delta as the l2 distance;
+ *    the method only ever compares distances, so squaring changes nothing).
+ *  - "Key order" is (squared distance, id) ascending.  It is the paper's
+ *    "ascending order of the distance" (Alg. 1, Alg. 2 line 8) with the
+ *    lower-index tie rule of the MRNG definition (Section 3.3) applied to
+ *    every tie.
+ *  - Pointers named *_dev are device pointers (cudaMalloc / torch CUDA
+ *    tensors); *_host are host pointers.  Matrices are dense row-major.
+ *    The caller owns every buffer it passes in; an nsg_index owns only what
+ *    it allocated itself and frees it in nsg_free().
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Unless stated otherwise a call only enqueues work on that
+ *    stream and returns; outputs are valid once the stream reaches them.
+ *  - Arguments are validated before anything is launched; a violation
+ *    returns NSG_EINVAL and touches nothing.  No call throws, aborts or
+ *    exits.  Ids are int32 (n < 2^31).  Unused output slots are filled with
+ *    id -1 and distance +inf.
+ *  - Every device loop has an iteration cap; hitting it never hangs the GPU:
+ *    the affected query reports NSG_ESTEPCAP in its status slot and keeps
+ *    the partial result.
+ */
+#ifndef NSG_H
+#define NSG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NSG_OK = 0,
+    NSG_EINVAL = -1,    /* invalid argument; nothing was launched */
+    NSG_ENOMEM = -2,    /* device or host allocation failed */
+    NSG_ECUDA = -3,     /* a CUDA runtime call failed (see nsg_last_cuda_error) */
+    NSG_ESTEPCAP = -4,  /* a search hit its step cap (partial result kept) */
+    NSG_EDEGREE = -5,   /* connectivity pass: no reached node has a free slot */
+    NSG_EIO = -6,       /* file could not be opened / read / written */
+    NSG_EFORMAT = -7    /* file is not an index written by nsg_save */
+} nsg_status;
+
+typedef struct nsg_index nsg_index; /* opaque; owns its device memory */
+
+/* Traversal precision of the search (the final pool is always re-ranked in
+ * FP32 when a low-precision copy is used). */
+typedef enum { NSG_PREC_F32 = 0, NSG_PREC_BF16 = 1, NSG_PREC_FP8 = 2 } nsg_precision;
+
+typedef struct {
+    int32_t max_steps;     /* expansion cap per query; <= 0 -> 16*L + 4096 */
+    int32_t hash_slots;    /* visited-hash slots per query (power of 2); <= 0 -> auto */
+    int32_t precision;     /* nsg_precision */
+    int32_t warps_per_cta; /* <= 0 -> auto */
+} nsg_search_params;
+
+typedef struct {
+    int64_t n;             /* base rows */
+    int32_t d;             /* dimension */
+    int32_t R;             /* adjacency width = max out-degree */
+    int32_t nav;           /* navigating node */
+    int32_t max_degree;    /* largest out-degree present */
+    double avg_degree;     /* mean out-degree (AOD of Table 2) */
+    int64_t n_fixup_edges; /* edges added by the connectivity pass */
+    int64_t device_bytes;  /* device memory held by the index */
+    int32_t has_bf16;      /* a BF16 copy of the base is held */
+    int32_t has_fp8;       /* an FP8-e4m3 copy of the base is held */
+    float fp8_scale;       /* x_fp8 = x * fp8_scale (0 when absent) */
+    /* build phase wall times in milliseconds (0 when not built here) */
+    float ms_knn, ms_centroid_nav, ms_collect, ms_prune, ms_connect, ms_total;
+} nsg_index_info_t;
+
+/* Human-readable name of a status code (static string). */
+const char *nsg_status_str(nsg_status s);
+/* Text of the last CUDA error seen by this library on the calling thread. */
+const char *nsg_last_cuda_error(void);
+
+/* ---------------------------------------------------------------------------
+ * A1. Brute-force kNN (serial scan, Section 4.1.2 item 1; Alg. 2 input G).
+ *
+ * nsg_knn_init: for every base row i, the K nearest OTHER rows in key order
+ *   (self excluded by id, so duplicate points stay neighbours).
+ *   base_dev [n][d] f32; knn_ids_dev [n][K] i32 out; knn_d2_dev [n][K] f32 out
+ *   (nullable).  Requires 1 <= K < n, d >= 1.  Uses tensor cores where the
+ *   data allows an exact answer, else an exact FP32 scan.  Allocates scratch.
+ * nsg_knn_query: the k nearest base rows of each query (ground truth):
+ *   queries_dev [nq][d]; ids_dev [nq][k]; d2_dev [nq][k] nullable; k <= n.
+ * ------------------------------------------------------------------------- */
+nsg_status nsg_knn_init(const float *base_dev, int64_t n, int32_t d, int32_t K,
+                        int32_t *knn_ids_dev, float *knn_d2_dev, void *stream);
+nsg_status nsg_knn_query(const float *base_dev, int64_t n, int32_t d, const float *queries_dev,
+                         int64_t nq, int32_t k, int32_t *ids_dev, float *d2_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * A2. Centroid (Alg. 2 line 1): c_j = (sum_i x_ij) / n, summed in FP64.
+ *   centroid_dev [d] f64 out.
+ * ------------------------------------------------------------------------- */
+nsg_status nsg_centroid(const float *base_dev, int64_t n, int32_t d, double *centroid_dev,
+                        void *stream);
+
+/* ---------------------------------------------------------------------------
+ * A3. Navigating node (Alg. 2 lines 2-3; Section 3.4 step ii): Alg. 1 on the
+ *   kNN graph from `start`, query = centroid, pool L; the navigating node is
+ *   the first pool entry.  Distances to the centroid are FP64, summed over j
+ *   in order without FMA contraction.  knn_ids_dev [n][K].
+ *   Synchronises the stream; *nav_host receives the node.
+ * ------------------------------------------------------------------------- */
+nsg_status nsg_navigate(const float *base_dev, int64_t n, int32_t d, const int32_t *knn_ids_dev,
+                        int32_t K, const double *centroid_dev, int32_t start, int32_t L,
+                        int32_t *nav_host, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * A5. Search-and-collect (Alg. 2 lines 5-8; Section 3.4 step iii; Fig. 4) for
+ *   nodes v0 .. v0+nv-1: Alg. 1 on the kNN graph from `nav` with query x_v
+ *   and pool L; every node whose distance was computed, plus v's K kNN
+ *   neighbours, minus v itself, sorted by key and cut to the C smallest.
+ *   base_dev [n][d] with d % 4 == 0 and 16-byte aligned rows.
+ *   cand_ids_dev [nv][C] i32, cand_d2_dev [nv][C] f32, cand_count_dev [nv]
+ *   i32 out (row j describes node v0 + j).  status_dev [nv] i32 nullable.
+ * ------------------------------------------------------------------------- */
+nsg_status nsg_collect(const float *base_dev, int64_t n, int32_t d, const int32_t *knn_ids_dev,
+                       int32_t K, int32_t nav, int32_t L, int32_t C, int64_t v0, int64_t nv,
+                       int32_t *cand_ids_dev, float *cand_d2_dev, int32_t *cand_count_dev,
+                       int32_t *status_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * A6. MRNG edge selection (Alg. 2 lines 9-20; Def. MRNG and Section 3.3) for
+ *   nodes v0 .. v0+nv-1 over their sorted candidates: the first candidate is
+ *   kept; a later candidate p is dropped when some kept r has
+ *   d2(p, r) < d2(p, v); stop at R kept.  Inputs as written by nsg_collect.
+ *   adj_dev [n][R] i32 and deg_dev [n] i32: rows v0.. are written (-1 padded).
+ * ------------------------------------------------------------------------- */
+nsg_status nsg_prune(const float *base_dev, int64_t n, int32_t d, const int32_t *cand_ids_dev,
+                     const float *cand_d2_dev, const int32_t *cand_count_dev, int32_t C, int32_t R,
+                     int64_t v0, int64_t nv, int32_t *adj_dev, int32_t *deg_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * A7. Connectivity (Alg. 2 lines 21-28; Section 3.4 step iv): reach from
+ *   `nav` (BFS; the same reached set as the paper's DFS tree).  While a node
+ *   is unreached: u = smallest unreached id; Alg. 1 on the current graph from
+ *   nav with query x_u and pool L; the first result (key order) whose
+ *   out-degree is below R gets the edge s->u appended (else the smallest
+ *   reached id with room; else NSG_EDEGREE); then everything reachable from
+ *   u is marked.  adj_dev / deg_dev are updated in place.
+ *   Synchronises the stream; *n_added_host receives the number of edges.
+ * ------------------------------------------------------------------------- */
+nsg_status nsg_connect(const float *base_dev, int64_t n, int32_t d, int32_t *adj_dev,
+                       int32_t *deg_dev, int32_t R, int32_t nav, int32_t L, int32_t *n_added_host,
+                       void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Whole Alg. 2: A1 (K) -> A2 -> A3 (start = splitmix64(seed) mod n, pool L)
+ *   -> A5/A6 for every node (L, C, R) -> A7 (L).  The base is copied into the
+ *   index (the caller may free base_dev afterwards).  Requires 1 <= K < n,
+ *   1 <= R <= C.  Synchronises the stream.
+ * ------------------------------------------------------------------------- */
+nsg_status nsg_build(const float *base_dev, int64_t n, int32_t d, int32_t K, int32_t L, int32_t R,
+                     int32_t C, uint64_t seed, void *stream, nsg_index **out);
+
+/* An index over a given graph (for searching a graph built elsewhere).
+ *   adj_dev [n][R] (-1 padded rows without repeated ids), deg_dev [n]
+ *   nullable (counted from adj when NULL).  Base and graph are copied. */
+nsg_status nsg_index_from_graph(const float *base_dev, int64_t n, int32_t d, const int32_t *adj_dev,
+                                const int32_t *deg_dev, int32_t R, int32_t nav, void *stream,
+                                nsg_index **out);
+
+/* ---------------------------------------------------------------------------
+ * A4. Search on NSG (Alg. 1 started at the navigating node, Section 3.5), one
+ *   warp per query: pool of L keys, expand the first unchecked entry, add its
+ *   unvisited out-neighbours, keep the L smallest keys, stop when every entry
+ *   is checked; return the first k.  queries_dev [nq][d] f32; ids_dev [nq][k]
+ *   i32 out; d2_dev [nq][k] f32 out (nullable).  1 <= k <= L <= 1024.
+ *   Returns NSG_ESTEPCAP (after the stream finishes) if any query hit its
+ *   cap -- nsg_search synchronises only in that check.
+ * nsg_search_ex: same with parameters and optional per-query outputs
+ *   n_expand_dev [nq] (nodes checked), n_dist_dev [nq] (distances computed),
+ *   status_dev [nq] (0 or NSG_ESTEPCAP).  Does not synchronise.
+ * ------------------------------------------------------------------------- */
+nsg_status nsg_search(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k,
+                      int32_t L, int32_t *ids_dev, float *d2_dev, void *stream);
+nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k,
+                         int32_t L, const nsg_search_params *params, int32_t *ids_dev,
+                         float *d2_dev, int32_t *n_expand_dev, int32_t *n_dist_dev,
+                         int32_t *status_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * A8. Precision (Eq. 1): hits_dev[q] = |{first k of ids} n {first k of gt}|.
+ *   ids_dev [nq][ld_ids], gt_dev [nq][ld_gt], hits_dev [nq] i32 out.
+ * ------------------------------------------------------------------------- */
+nsg_status nsg_recall(const int32_t *ids_dev, int32_t ld_ids, const int32_t *gt_dev, int32_t ld_gt,
+                      int64_t nq, int32_t k, int32_t *hits_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Index management.
+ * nsg_index_info: sizes, navigating node, degree statistics, build times.
+ * nsg_index_graph: copy the adjacency [n][R] and degrees [n] to device
+ *   buffers (either nullable); async on stream.
+ * nsg_save / nsg_load: little-endian file: magic "NSGGB300", version, n, d,
+ *   R, nav, then deg [n] i32, adj [n][R] i32, base [n][d] f32.  Synchronous.
+ * nsg_free: releases the index (NULL is ignored).
+ * ------------------------------------------------------------------------- */
+nsg_status nsg_index_info(const nsg_index *idx, nsg_index_info_t *info);
+nsg_status nsg_index_graph(const nsg_index *idx, int32_t *adj_dev, int32_t *deg_dev, void *stream);
+nsg_status nsg_save(const nsg_index *idx, const char *path);
+nsg_status nsg_load(const char *path, void *stream, nsg_index **out);
+void nsg_free(nsg_index *idx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NSG_H */

@@ -1,0 +1,273 @@
+"""Thin ctypes binding of ``libnsg.so`` (declared in ``include/nsg.h``).
+
+Argument marshalling only: tensors become raw device pointers, the current
+torch stream becomes the ``stream`` argument, status codes become
+exceptions.  Every step of the method runs in the library's CUDA kernels.
+There is no CPU fallback: if the library is missing or no GPU is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnsg.so")
+
+NSG_OK, NSG_EINVAL, NSG_ENOMEM, NSG_ECUDA, NSG_ESTEPCAP, NSG_EDEGREE, NSG_EIO, NSG_EFORMAT = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+PREC_F32, PREC_BF16, PREC_FP8 = 0, 1, 2
+
+
+class NsgError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = lib().nsg_status_str(status).decode()
+        if status == NSG_ECUDA:
+            msg += " (" + lib().nsg_last_cuda_error().decode() + ")"
+        super().__init__(f"{where}: {msg}")
+
+
+class SearchParams(C.Structure):
+    _fields_ = [("max_steps", C.c_int32), ("hash_slots", C.c_int32), ("precision", C.c_int32),
+                ("warps_per_cta", C.c_int32)]
+
+
+class IndexInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("R", C.c_int32), ("nav", C.c_int32),
+                ("max_degree", C.c_int32), ("avg_degree", C.c_double), ("n_fixup_edges", C.c_int64),
+                ("device_bytes", C.c_int64), ("has_bf16", C.c_int32), ("has_fp8", C.c_int32),
+                ("fp8_scale", C.c_float), ("ms_knn", C.c_float), ("ms_centroid_nav", C.c_float),
+                ("ms_collect", C.c_float), ("ms_prune", C.c_float), ("ms_connect", C.c_float),
+                ("ms_total", C.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+P, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+
+# (name, argtypes, restype) of every exported symbol -- the same list as include/nsg.h
+SIGNATURES = [
+    ("nsg_status_str", [i32], C.c_char_p),
+    ("nsg_last_cuda_error", [], C.c_char_p),
+    ("nsg_knn_init", [P, i64, i32, i32, P, P, P], i32),
+    ("nsg_knn_query", [P, i64, i32, P, i64, i32, P, P, P], i32),
+    ("nsg_centroid", [P, i64, i32, P, P], i32),
+    ("nsg_navigate", [P, i64, i32, P, i32, P, i32, i32, P, P], i32),
+    ("nsg_collect", [P, i64, i32, P, i32, i32, i32, i32, i64, i64, P, P, P, P, P], i32),
+    ("nsg_prune", [P, i64, i32, P, P, P, i32, i32, i64, i64, P, P, P], i32),
+    ("nsg_connect", [P, i64, i32, P, P, i32, i32, i32, P, P], i32),
+    ("nsg_build", [P, i64, i32, i32, i32, i32, i32, u64, P, P], i32),
+    ("nsg_index_from_graph", [P, i64, i32, P, P, i32, i32, P, P], i32),
+    ("nsg_search", [P, P, i64, i32, i32, P, P, P], i32),
+    ("nsg_search_ex", [P, P, i64, i32, i32, P, P, P, P, P, P, P], i32),
+    ("nsg_recall", [P, i32, P, i32, i64, i32, P, P], i32),
+    ("nsg_index_info", [P, P], i32),
+    ("nsg_index_graph", [P, P, P, P], i32),
+    ("nsg_save", [P, C.c_char_p], i32),
+    ("nsg_load", [C.c_char_p, P, P], i32),
+    ("nsg_free", [P], None),
+]
+
+
+def lib():
+    """Load libnsg.so (built by ``paper_1707_00143_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1707_00143_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, args, res in SIGNATURES:
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc != NSG_OK:
+        raise NsgError(rc, where)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, dtype):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor")
+    return t
+
+
+def nsg_knn_init(base, K, with_d2=True):
+    base = _dev(base, torch.float32)
+    n, d = base.shape
+    ids = torch.empty((n, K), dtype=torch.int32, device=base.device)
+    d2 = torch.empty((n, K), dtype=torch.float32, device=base.device) if with_d2 else None
+    _check(lib().nsg_knn_init(_ptr(base), n, d, K, _ptr(ids), _ptr(d2), _stream()), "nsg_knn_init")
+    return ids, d2
+
+
+def nsg_knn_query(base, queries, k):
+    base, queries = _dev(base, torch.float32), _dev(queries, torch.float32)
+    n, d = base.shape
+    nq = queries.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int32, device=base.device)
+    d2 = torch.empty((nq, k), dtype=torch.float32, device=base.device)
+    _check(lib().nsg_knn_query(_ptr(base), n, d, _ptr(queries), nq, k, _ptr(ids), _ptr(d2), _stream()),
+           "nsg_knn_query")
+    return ids, d2
+
+
+def nsg_centroid(base):
+    base = _dev(base, torch.float32)
+    n, d = base.shape
+    c = torch.empty(d, dtype=torch.float64, device=base.device)
+    _check(lib().nsg_centroid(_ptr(base), n, d, _ptr(c), _stream()), "nsg_centroid")
+    return c
+
+
+def nsg_navigate(base, knn, centroid, start, L):
+    base, knn = _dev(base, torch.float32), _dev(knn, torch.int32)
+    centroid = _dev(centroid, torch.float64)
+    n, d = base.shape
+    nav = C.c_int32(0)
+    _check(lib().nsg_navigate(_ptr(base), n, d, _ptr(knn), knn.shape[1], _ptr(centroid), int(start), L,
+                              C.byref(nav), _stream()), "nsg_navigate")
+    return nav.value
+
+
+def nsg_collect(base, knn, nav, L, Cap, v0=0, nv=None):
+    base, knn = _dev(base, torch.float32), _dev(knn, torch.int32)
+    n, d = base.shape
+    nv = n - v0 if nv is None else nv
+    dev = base.device
+    ids = torch.empty((nv, Cap), dtype=torch.int32, device=dev)
+    d2 = torch.empty((nv, Cap), dtype=torch.float32, device=dev)
+    cnt = torch.empty(nv, dtype=torch.int32, device=dev)
+    st = torch.empty(nv, dtype=torch.int32, device=dev)
+    _check(lib().nsg_collect(_ptr(base), n, d, _ptr(knn), knn.shape[1], int(nav), L, Cap, v0, nv,
+                             _ptr(ids), _ptr(d2), _ptr(cnt), _ptr(st), _stream()), "nsg_collect")
+    return ids, d2, cnt, st
+
+
+def nsg_prune(base, cand_ids, cand_d2, cand_count, R, v0=0, adj=None, deg=None):
+    base = _dev(base, torch.float32)
+    n, d = base.shape
+    nv, Cap = cand_ids.shape
+    dev = base.device
+    adj = torch.full((n, R), -1, dtype=torch.int32, device=dev) if adj is None else adj
+    deg = torch.zeros(n, dtype=torch.int32, device=dev) if deg is None else deg
+    _check(lib().nsg_prune(_ptr(base), n, d, _ptr(_dev(cand_ids, torch.int32)),
+                           _ptr(_dev(cand_d2, torch.float32)), _ptr(_dev(cand_count, torch.int32)),
+                           Cap, R, v0, nv, _ptr(adj), _ptr(deg), _stream()), "nsg_prune")
+    return adj, deg
+
+
+def nsg_connect(base, adj, deg, nav, L):
+    base = _dev(base, torch.float32)
+    adj, deg = _dev(adj, torch.int32), _dev(deg, torch.int32)
+    n, d = base.shape
+    added = C.c_int32(0)
+    _check(lib().nsg_connect(_ptr(base), n, d, _ptr(adj), _ptr(deg), adj.shape[1], int(nav), L,
+                             C.byref(added), _stream()), "nsg_connect")
+    return added.value
+
+
+def nsg_recall(ids, gt, k):
+    ids, gt = _dev(ids, torch.int32), _dev(gt, torch.int32)
+    hits = torch.empty(ids.shape[0], dtype=torch.int32, device=ids.device)
+    _check(lib().nsg_recall(_ptr(ids), ids.shape[1], _ptr(gt), gt.shape[1], ids.shape[0], k, _ptr(hits),
+                            _stream()), "nsg_recall")
+    return hits
+
+
+class Index:
+    """Owner of an ``nsg_index*`` (freed with the object or by ``free()``)."""
+
+    def __init__(self, handle):
+        self.h = handle
+
+    def free(self):
+        if self.h:
+            lib().nsg_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self):
+        inf = IndexInfo()
+        _check(lib().nsg_index_info(self.h, C.byref(inf)), "nsg_index_info")
+        return inf.as_dict()
+
+    def graph(self):
+        inf = self.info()
+        adj = torch.empty((inf["n"], inf["R"]), dtype=torch.int32, device="cuda")
+        deg = torch.empty(inf["n"], dtype=torch.int32, device="cuda")
+        _check(lib().nsg_index_graph(self.h, _ptr(adj), _ptr(deg), _stream()), "nsg_index_graph")
+        return adj, deg
+
+    def search(self, queries, k, L):
+        queries = _dev(queries, torch.float32)
+        nq = queries.shape[0]
+        ids = torch.empty((nq, k), dtype=torch.int32, device=queries.device)
+        d2 = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+        _check(lib().nsg_search(self.h, _ptr(queries), nq, k, L, _ptr(ids), _ptr(d2), _stream()),
+               "nsg_search")
+        return ids, d2
+
+    def search_ex(self, queries, k, L, params=None, out=None, counters=True):
+        queries = _dev(queries, torch.float32)
+        nq = queries.shape[0]
+        dev = queries.device
+        if out is None:
+            out = dict(ids=torch.empty((nq, k), dtype=torch.int32, device=dev),
+                       d2=torch.empty((nq, k), dtype=torch.float32, device=dev))
+            if counters:
+                out.update(n_expand=torch.empty(nq, dtype=torch.int32, device=dev),
+                           n_dist=torch.empty(nq, dtype=torch.int32, device=dev),
+                           status=torch.empty(nq, dtype=torch.int32, device=dev))
+        p = params if params is not None else SearchParams(0, 0, PREC_F32, 0)
+        _check(lib().nsg_search_ex(self.h, _ptr(queries), nq, k, L, C.byref(p), _ptr(out["ids"]),
+                                   _ptr(out.get("d2")), _ptr(out.get("n_expand")), _ptr(out.get("n_dist")),
+                                   _ptr(out.get("status")), _stream()), "nsg_search_ex")
+        return out
+
+    def save(self, path):
+        _check(lib().nsg_save(self.h, path.encode()), "nsg_save")
+
+
+def nsg_build(base, K, L, R, Cap, seed=0):
+    base = _dev(base, torch.float32)
+    n, d = base.shape
+    h = C.c_void_p()
+    _check(lib().nsg_build(_ptr(base), n, d, K, L, R, Cap, seed, _stream(), C.byref(h)), "nsg_build")
+    return Index(h)
+
+
+def nsg_index_from_graph(base, adj, nav, deg=None):
+    base, adj = _dev(base, torch.float32), _dev(adj, torch.int32)
+    n, d = base.shape
+    h = C.c_void_p()
+    _check(lib().nsg_index_from_graph(_ptr(base), n, d, _ptr(adj), _ptr(deg), adj.shape[1], int(nav),
+                                      _stream(), C.byref(h)), "nsg_index_from_graph")
+    return Index(h)
+
+
+def nsg_load(path):
+    h = C.c_void_p()
+    _check(lib().nsg_load(path.encode(), _stream(), C.byref(h)), "nsg_load")
+    return Index(h)

@@ -1,0 +1,510 @@
+// build.cu -- Alg. 2 kernels other than the per-node search: centroid (line 1),
+// navigating node (lines 2-3), MRNG edge selection (lines 9-20), reachability
+// and the connectivity pass (lines 21-28); plus the precision count (Eq. 1)
+// and a row-padding copy.
+#include <climits>
+
+#include "kernels.h"
+#include "search_core.cuh"
+
+namespace nsg {
+
+__host__ __device__ static inline int round32(int x) { return (x + 31) & ~31; }
+static inline int log2i(unsigned x) {
+    int r = 0;
+    while ((1u << r) < x) ++r;
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_volatile(const T *p) {
+    return *reinterpret_cast<const volatile T *>(p);
+}
+
+// ---------------------------------------------------------------------------
+// Centroid (Alg. 2 line 1): block b sums rows [b*rows, (b+1)*rows) of every
+// column in FP64 (row order), then one pass adds the block sums in block order
+// and divides by n.  On integer data every partial sum is exact.
+// ---------------------------------------------------------------------------
+__global__ void centroid_partial_kernel(const float *__restrict__ base, int64_t n, int d,
+                                        int64_t rows, double *__restrict__ partial) {
+    const int64_t r0 = (int64_t)blockIdx.x * rows;
+    const int64_t r1 = r0 + rows < n ? r0 + rows : n;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        double s = 0.0;
+        for (int64_t r = r0; r < r1; ++r) s = __dadd_rn(s, (double)__ldg(base + r * d + j));
+        partial[(int64_t)blockIdx.x * d + j] = s;
+    }
+}
+
+__global__ void centroid_final_kernel(const double *__restrict__ partial, int nb, int d, int64_t n,
+                                      double *__restrict__ c) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s = __dadd_rn(s, partial[(int64_t)b * d + j]);
+        c[j] = __ddiv_rn(s, (double)n);
+    }
+}
+
+cudaError_t launch_centroid(const float *base, int64_t n, int d, double *partial, int nblocks,
+                            double *c, cudaStream_t st) {
+    int64_t rows = (n + nblocks - 1) / nblocks;
+    int nb = (int)((n + rows - 1) / rows);
+    int threads = d < 256 ? round32(d) : 256;
+    centroid_partial_kernel<<<nb, threads, 0, st>>>(base, n, d, rows, partial);
+    centroid_final_kernel<<<(d + 255) / 256, 256, 0, st>>>(partial, nb, d, n, c);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Navigating node (Alg. 2 lines 2-3): Alg. 1 on the kNN graph from `start`
+// toward the centroid, one warp.  Distances are FP64 sums over j in order with
+// explicitly rounded operations (no FMA), so they do not depend on the
+// compiler.  Lanes compute the distances of the new neighbours; lane 0 keeps
+// the sorted pool (one query: simplicity over speed).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool dkey_less(double da, int ia, double db, int ib) {
+    return da < db || (da == db && ia < ib);
+}
+
+__global__ void navigate_kernel(const float *__restrict__ base, int d, const int *__restrict__ knn,
+                                int K, const double *__restrict__ cg, int start, int L,
+                                uint32_t *visited, int max_steps, int *nav_out, int *status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int Wk = round32(K);
+    double *c = reinterpret_cast<double *>(smem);
+    double *pd = c + d;
+    double *cd = pd + (L + 1);
+    int *pid = reinterpret_cast<int *>(cd + Wk);
+    int *pchk = pid + (L + 1);
+    int *cid = pchk + (L + 1);
+    const unsigned lane = threadIdx.x & 31;
+    for (int j = lane; j < d; j += 32) c[j] = cg[j];
+    __syncwarp();
+    auto dist = [&](int id) -> double {
+        const float *x = base + (int64_t)id * d;
+        double s = 0.0;
+        for (int j = 0; j < d; ++j) {
+            double t = __dsub_rn((double)__ldg(x + j), c[j]);
+            s = __dadd_rn(s, __dmul_rn(t, t));
+        }
+        return s;
+    };
+    int size = 1;
+    if (lane == 0) {
+        atomicOr(visited + (start >> 5), 1u << (start & 31));
+        pd[0] = dist(start);
+        pid[0] = start;
+        pchk[0] = 0;
+    }
+    __syncwarp();
+    int steps = 0;
+    bool capped = false;
+    for (;;) {
+        int i = -1;
+        if (lane == 0)
+            for (int t = 0; t < size; ++t)
+                if (!pchk[t]) {
+                    i = t;
+                    break;
+                }
+        i = __shfl_sync(NSG_FULL, i, 0);
+        if (i < 0) break;
+        if (steps >= max_steps) {
+            capped = true;
+            break;
+        }
+        ++steps;
+        if (lane == 0) pchk[i] = 1;
+        __syncwarp();
+        const int u = pid[i];
+        int m = 0;
+        for (int b = 0; b < K; b += 32) {
+            int slot = b + lane;
+            int w = slot < K ? __ldg(knn + (int64_t)u * K + slot) : -1;
+            bool fresh = false;
+            if (w >= 0) {
+                uint32_t bit = 1u << (w & 31);
+                fresh = !(atomicOr(visited + (w >> 5), bit) & bit);
+            }
+            unsigned bal = __ballot_sync(NSG_FULL, fresh);
+            if (fresh) cid[m + __popc(bal & lanemask_lt())] = w;
+            m += __popc(bal);
+        }
+        __syncwarp();
+        for (int t = lane; t < m; t += 32) cd[t] = dist(cid[t]);
+        __syncwarp();
+        if (lane == 0) {
+            for (int t = 0; t < m; ++t) {
+                double dv = cd[t];
+                int iv = cid[t];
+                if (size == L && !dkey_less(dv, iv, pd[L - 1], pid[L - 1])) continue;
+                int pos = size < L ? size : L - 1;
+                while (pos > 0 && dkey_less(dv, iv, pd[pos - 1], pid[pos - 1])) {
+                    pd[pos] = pd[pos - 1];
+                    pid[pos] = pid[pos - 1];
+                    pchk[pos] = pchk[pos - 1];
+                    --pos;
+                }
+                pd[pos] = dv;
+                pid[pos] = iv;
+                pchk[pos] = 0;
+                if (size < L) ++size;
+            }
+        }
+        size = __shfl_sync(NSG_FULL, size, 0);
+        __syncwarp();
+    }
+    if (lane == 0) {
+        *nav_out = pid[0];
+        *status = capped ? -4 : 0;
+    }
+}
+
+cudaError_t launch_navigate(const float *base, int64_t n, int d, const int *knn, int K,
+                            const double *c, int start, int L, uint32_t *visited_bits,
+                            int max_steps, int *nav_out, int *status, cudaStream_t st) {
+    (void)n;
+    int Wk = round32(K);
+    size_t smem = 8ull * (d + (L + 1) + Wk) + 4ull * (2 * (L + 1) + Wk);
+    cudaError_t e = cudaFuncSetAttribute(navigate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    navigate_kernel<<<1, 32, smem, st>>>(base, d, knn, K, c, start, L, visited_bits, max_steps,
+                                         nav_out, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// MRNG edge selection (Alg. 2 lines 9-20), one warp per node.  Candidates are
+// already sorted by key; the first is kept; a later candidate p is occluded
+// when d2(p, r) < d2(p, v) for a kept r (r in the open lune of vp); stop at R.
+// The warp holds p's row; G-lane groups compute d2(p, r) for the kept rows.
+// ---------------------------------------------------------------------------
+struct PruneArgs {
+    const float4 *base4;
+    int dp4;
+    const int *cand_ids;
+    const float *cand_d2;
+    const int *cand_count;
+    int C, R, Wr;
+    int64_t v0, nv;
+    int *adj, *deg;
+};
+
+template <int G, int V, int U>
+__global__ void __launch_bounds__(256) prune_kernel(PruneArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const unsigned lane = lane_id();
+    uint64_t *keys = reinterpret_cast<uint64_t *>(smem) + (size_t)warp * a.Wr;
+    int *kept = reinterpret_cast<int *>(reinterpret_cast<uint64_t *>(smem) + (size_t)wpb * a.Wr) +
+                (size_t)warp * a.Wr;
+    const int64_t stride = (int64_t)gridDim.x * wpb;
+    for (int64_t j = (int64_t)blockIdx.x * wpb + warp; j < a.nv; j += stride) {
+        const int64_t v = a.v0 + j;
+        const int *ci = a.cand_ids + j * a.C;
+        const float *cd = a.cand_d2 + j * a.C;
+        const int cnt = min(max(a.cand_count[j], 0), a.C);
+        int nk = 0;
+        if (cnt > 0) {
+            if (lane == 0) kept[0] = ci[0];
+            nk = 1;
+        }
+        __syncwarp();
+        for (int t = 1; t < cnt && nk < a.R; ++t) {
+            const int p = ci[t];
+            const float dpv = cd[t];
+            RowQuery<G, V> P;
+            P.load_row(a.base4 + (int64_t)p * a.dp4, a.dp4);
+            rows_dist<G, V, U>(P, a.base4, a.dp4, kept, nk, keys);
+            bool occ = false;
+            for (int b = lane; b < nk; b += 32) occ |= kd2(keys[b]) < dpv;
+            if (!__any_sync(NSG_FULL, occ)) {
+                if (lane == 0) kept[nk] = p;
+                ++nk;
+                __syncwarp();
+            }
+        }
+        for (int t = lane; t < a.R; t += 32) a.adj[v * a.R + t] = t < nk ? kept[t] : -1;
+        if (lane == 0) a.deg[v] = nk;
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_prune(const PruneLaunch &l, cudaStream_t st) {
+    if (l.nv <= 0) return cudaSuccess;
+    PruneArgs a;
+    a.base4 = reinterpret_cast<const float4 *>(l.base);
+    a.dp4 = l.dp / 4;
+    a.cand_ids = l.cand_ids;
+    a.cand_d2 = l.cand_d2;
+    a.cand_count = l.cand_count;
+    a.C = l.C;
+    a.R = l.R;
+    a.Wr = round32(l.R);
+    a.v0 = l.v0;
+    a.nv = l.nv;
+    a.adj = l.adj;
+    a.deg = l.deg;
+    const int wpb = 8;
+    size_t smem = (size_t)wpb * a.Wr * 12;
+    cudaError_t err = cudaSuccess;
+    NSG_DISPATCH_DP4(a.dp4, {
+        auto kern = prune_kernel<G_, V_, U_>;
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess) {
+            int per_sm = 0;
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
+            if (err == cudaSuccess) {
+                int64_t need = (l.nv + wpb - 1) / wpb;
+                int64_t full = (int64_t)sm_count() * (per_sm > 0 ? per_sm : 1);
+                int grid = (int)(need < full ? need : full);
+                kern<<<grid, wpb * 32, smem, st>>>(a);
+                err = cudaGetLastError();
+            }
+        }
+    });
+    return err;
+}
+
+// ---------------------------------------------------------------------------
+// Reachability from the navigating node: level-synchronous BFS over the
+// fixed-width graph (the reached set equals that of the paper's DFS tree).
+// ---------------------------------------------------------------------------
+__global__ void bfs_seed_kernel(uint32_t *reached, int root, int *frontier, int *count) {
+    atomicOr(reached + (root >> 5), 1u << (root & 31));
+    frontier[0] = root;
+    *count = 1;
+}
+
+__global__ void bfs_level_kernel(const int *__restrict__ adj, int R, const int *__restrict__ frontier,
+                                 int nf, int *next, int *next_count, uint32_t *reached) {
+    const int64_t total = (int64_t)nf * R;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int u = frontier[x / R];
+        int v = adj[(int64_t)u * R + x % R];
+        if (v < 0) continue;
+        uint32_t bit = 1u << (v & 31);
+        if (!(atomicOr(reached + (v >> 5), bit) & bit)) next[atomicAdd(next_count, 1)] = v;
+    }
+}
+
+cudaError_t launch_bfs_seed(uint32_t *reached, int root, int *frontier, int *count, cudaStream_t st) {
+    bfs_seed_kernel<<<1, 1, 0, st>>>(reached, root, frontier, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bfs_level(const int *adj, int R, const int *frontier, int nf, int *next,
+                             int *next_count, uint32_t *reached, cudaStream_t st) {
+    int64_t total = (int64_t)nf * R;
+    int64_t blocks = (total + 255) / 256;
+    int64_t cap = (int64_t)sm_count() * 8;
+    bfs_level_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, st>>>(adj, R, frontier, nf, next,
+                                                                         next_count, reached);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Connectivity pass (Alg. 2 lines 21-28), one CTA of 8 warps that loops
+// until every node is reached: smallest unreached id u -> warp 0 runs Alg. 1
+// on the current graph from nav toward x_u -> first result with a free slot
+// (else the smallest reached id with one) gets s->u -> the CTA marks what u
+// reaches.  The graph is edited by this kernel, so it is read with volatile
+// (coherent) loads; __syncthreads orders the CTA's global writes.
+// ---------------------------------------------------------------------------
+struct ConnectArgs {
+    const float4 *base4;
+    int dp4;
+    int64_t n;
+    int *adj, *deg;
+    int R, W, nav, L, H, hshift, max_steps;
+    uint32_t *reached;
+    int *queue, *out;
+};
+
+template <int G, int V, int U>
+__global__ void __launch_bounds__(256) connect_kernel(ConnectArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int sh_found, sh_size, sh_sel, sh_qtail, sh_capped;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    WarpSmem s = carve_warp_smem(smem, a.L, a.W, 0, a.H);
+    const int64_t nwords = (a.n + 31) >> 5;
+    const int tailbits = (int)(a.n & 31);
+    int64_t cursor = 0;
+    int added = 0, status = 0;
+    if (tid == 0) sh_capped = 0;
+    for (int64_t iter = 0; iter <= a.n; ++iter) {
+        if (tid == 0) sh_found = INT_MAX;
+        __syncthreads();
+        for (int64_t w0 = cursor; w0 < nwords; w0 += blockDim.x) {
+            int64_t w = w0 + tid;
+            if (w < nwords) {
+                uint32_t bits = ld_volatile(a.reached + w);
+                if (w == nwords - 1 && tailbits) bits |= ~((1u << tailbits) - 1u);
+                if (bits != 0xffffffffu) atomicMin(&sh_found, (int)(w * 32 + __ffs(~bits) - 1));
+            }
+            __syncthreads();
+            int f = sh_found;
+            __syncthreads();
+            if (f != INT_MAX) break;
+        }
+        const int u = sh_found;
+        if (u == INT_MAX) break;
+        cursor = u >> 5;
+        if (warp == 0) {
+            RowQuery<G, V> Q;
+            Q.load_row(a.base4 + (int64_t)u * a.dp4, a.dp4);
+            int csize = 0;
+            SearchOut o = warp_alg1<G, V, U, false, true>(Q, a.base4, a.dp4, GraphRef{a.adj, a.R}, a.nav,
+                                                           a.L, s, (uint32_t)a.H - 1, a.hshift,
+                                                           a.max_steps, -1, 0, csize);
+            if (lane_id() == 0) {
+                sh_size = o.size;
+                if (o.capped) sh_capped = 1;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int sel = -1;
+            for (int t = 0; t < sh_size; ++t) {
+                int id = kid(s.pool[t]);
+                if (ld_volatile(a.deg + id) < a.R) {
+                    sel = id;
+                    break;
+                }
+            }
+            sh_sel = sel;
+            sh_found = INT_MAX;
+        }
+        __syncthreads();
+        if (sh_sel < 0) {
+            for (int64_t x = tid; x < a.n; x += blockDim.x) {
+                uint32_t bits = ld_volatile(a.reached + (x >> 5));
+                if (((bits >> (x & 31)) & 1u) && ld_volatile(a.deg + x) < a.R) atomicMin(&sh_found, (int)x);
+            }
+            __syncthreads();
+            if (tid == 0) sh_sel = sh_found == INT_MAX ? -1 : sh_found;
+            __syncthreads();
+            if (sh_sel < 0) {
+                status = -5;
+                break;
+            }
+        }
+        if (tid == 0) {
+            const int sel = sh_sel;
+            const int dg = a.deg[sel];
+            a.adj[(int64_t)sel * a.R + dg] = u;
+            a.deg[sel] = dg + 1;
+            atomicOr(a.reached + (u >> 5), 1u << (u & 31));
+            a.queue[0] = u;
+            sh_qtail = 1;
+        }
+        ++added;
+        __syncthreads();
+        int head = 0;
+        for (;;) {
+            const int tail = sh_qtail;
+            if (head == tail) break;
+            __syncthreads();
+            const int64_t total = (int64_t)(tail - head) * a.R;
+            for (int64_t x = tid; x < total; x += blockDim.x) {
+                int node = ld_volatile(a.queue + head + x / a.R);
+                int v = ld_volatile(a.adj + (int64_t)node * a.R + x % a.R);
+                if (v < 0) continue;
+                uint32_t bit = 1u << (v & 31);
+                if (!(atomicOr(a.reached + (v >> 5), bit) & bit)) a.queue[atomicAdd(&sh_qtail, 1)] = v;
+            }
+            head = tail;
+            __syncthreads();
+        }
+    }
+    if (tid == 0) {
+        a.out[0] = added;
+        a.out[1] = status;
+        a.out[2] = sh_capped;
+    }
+}
+
+cudaError_t launch_connect(const ConnectLaunch &l, cudaStream_t st) {
+    ConnectArgs a;
+    a.base4 = reinterpret_cast<const float4 *>(l.base);
+    a.dp4 = l.dp / 4;
+    a.n = l.n;
+    a.adj = l.adj;
+    a.deg = l.deg;
+    a.R = l.R;
+    a.W = round32(l.R);
+    a.nav = l.nav;
+    a.L = l.L;
+    a.H = l.hash_slots;
+    a.hshift = 32 - log2i((unsigned)l.hash_slots);
+    a.max_steps = l.max_steps;
+    a.reached = l.reached;
+    a.queue = l.queue;
+    a.out = l.out;
+    size_t smem = warp_smem_bytes(a.L, a.W, 0, a.H);
+    cudaError_t err = cudaSuccess;
+    NSG_DISPATCH_DP4(a.dp4, {
+        auto kern = connect_kernel<G_, V_, U_>;
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess) {
+            kern<<<1, 256, smem, st>>>(a);
+            err = cudaGetLastError();
+        }
+    });
+    return err;
+}
+
+// ---------------------------------------------------------------------------
+// Precision (Eq. 1): per query, how many of the first k ids are among the
+// first k ground-truth ids.
+// ---------------------------------------------------------------------------
+__global__ void recall_kernel(const int *__restrict__ ids, int ld_ids, const int *__restrict__ gt,
+                              int ld_gt, int64_t nq, int k, int *hits) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int h = 0;
+        for (int a = 0; a < k; ++a) {
+            int id = ids[q * ld_ids + a];
+            if (id < 0) continue;
+            for (int b = 0; b < k; ++b)
+                if (gt[q * ld_gt + b] == id) {
+                    ++h;
+                    break;
+                }
+        }
+        hits[q] = h;
+    }
+}
+
+cudaError_t launch_recall(const int *ids, int ld_ids, const int *gt, int ld_gt, int64_t nq, int k,
+                          int *hits, cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    int64_t blocks = (nq + 255) / 256;
+    recall_kernel<<<(int)(blocks < 65535 ? blocks : 65535), 256, 0, st>>>(ids, ld_ids, gt, ld_gt, nq,
+                                                                           k, hits);
+    return cudaGetLastError();
+}
+
+__global__ void pad_rows_kernel(const float *__restrict__ src, int64_t n, int d, float *__restrict__ dst,
+                                int dp) {
+    const int64_t total = n * dp;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = x / dp;
+        int c = (int)(x % dp);
+        dst[x] = c < d ? src[r * d + c] : 0.0f;
+    }
+}
+
+cudaError_t launch_pad_rows(const float *src, int64_t n, int d, float *dst, int dp, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n * dp + 255) / 256;
+    int64_t cap = (int64_t)sm_count() * 16;
+    pad_rows_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, st>>>(src, n, d, dst, dp);
+    return cudaGetLastError();
+}
+
+}  // namespace nsg

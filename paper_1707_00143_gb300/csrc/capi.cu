@@ -1,0 +1,786 @@
+// capi.cu -- the extern "C" entry points declared in include/nsg.h.
+//
+// Host code here only validates arguments, owns index memory and sequences
+// launches; every step of the method runs in the kernels of search.cu,
+// build.cu and knn.cu.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "kernels.h"
+#include "nsg.h"
+
+struct nsg_index {
+    int64_t n = 0;
+    int d = 0, dp = 0, R = 0, nav = 0;
+    float *base = nullptr;  // [n][dp], zero padded
+    int *adj = nullptr;     // [n][R], -1 padded
+    int *deg = nullptr;     // [n]
+    int *flag = nullptr;    // [4] device scratch for nsg_search's cap check
+    int max_degree = 0;
+    double avg_degree = 0.0;
+    int64_t n_fixup = 0;
+    float ms[6] = {0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+nsg_status cuda_fail(cudaError_t e, const char *what) {
+    std::snprintf(g_err, sizeof(g_err), "%s: %s", what, cudaGetErrorString(e));
+    return NSG_ECUDA;
+}
+
+#define NSG_CK(x)                                                \
+    do {                                                         \
+        cudaError_t e_ = (x);                                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #x);         \
+    } while (0)
+
+// RAII device buffer for scratch and index members under construction.
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t count) {
+        if (p) cudaFree(p);
+        p = nullptr;
+        return cudaMalloc(reinterpret_cast<void **>(&p), count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    }
+    T *release() {
+        T *q = p;
+        p = nullptr;
+        return q;
+    }
+};
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+inline int round_up4(int d) { return (d + 3) & ~3; }
+inline unsigned next_pow2(unsigned x) {
+    unsigned p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+inline int default_hash(int L, int width) {
+    unsigned h = next_pow2((unsigned)L * (unsigned)width);
+    if (h < 1024) h = 1024;
+    if (h > 8192) h = 8192;
+    return (int)h;
+}
+inline int default_steps(int L) { return 16 * L + 4096; }
+inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Published SplitMix64 finaliser (Steele, Lea, Flood 2014): the random start
+// node of Alg. 2 line 2 is splitmix64(seed) mod n.
+inline uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+__global__ void check_ids_kernel(const int *ids, int64_t count, int64_t n, int *bad) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < count;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int v = ids[x];
+        if (v < -1 || v >= n) atomicOr(bad, 1);
+    }
+}
+
+// Every id in [-1, n)?  Guards the gather kernels against out-of-range reads.
+nsg_status check_ids(const int *ids, int64_t count, int64_t n, cudaStream_t st) {
+    if (count <= 0) return NSG_OK;
+    DevBuf<int> bad;
+    NSG_CK(bad.alloc(1));
+    NSG_CK(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+    int64_t blocks = (count + 255) / 256;
+    int64_t cap = (int64_t)nsg::sm_count() * 8;
+    check_ids_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, st>>>(ids, count, n, bad.p);
+    NSG_CK(cudaGetLastError());
+    int h = 0;
+    NSG_CK(cudaMemcpyAsync(&h, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NSG_CK(cudaStreamSynchronize(st));
+    return h ? NSG_EINVAL : NSG_OK;
+}
+
+// Copy [n][d] into a fresh zero-padded [n][dp] buffer.
+nsg_status padded_copy(const float *src, int64_t n, int d, int dp, DevBuf<float> &dst, cudaStream_t st) {
+    NSG_CK(dst.alloc((size_t)n * dp));
+    NSG_CK(nsg::launch_pad_rows(src, n, d, dst.p, dp, st));
+    return NSG_OK;
+}
+
+// Returns a [n][dp] view: the input itself when already padded and aligned.
+nsg_status padded_view(const float *src, int64_t n, int d, DevBuf<float> &tmp, const float **view,
+                       cudaStream_t st) {
+    if ((d & 3) == 0 && aligned16(src)) {
+        *view = src;
+        return NSG_OK;
+    }
+    nsg_status s = padded_copy(src, n, d, round_up4(d), tmp, st);
+    *view = tmp.p;
+    return s;
+}
+
+nsg_status knn_run(const float *bp, int64_t n, int dp, const float *qp, int64_t nq, int64_t q0, int k,
+                   int self_join, int *ids, float *d2, cudaStream_t st) {
+    nsg::KnnLaunch l;
+    l.base = bp;
+    l.n = n;
+    l.dp = dp;
+    l.queries = qp;
+    l.nq = nq;
+    l.q0 = q0;
+    l.k = k;
+    l.self_join = self_join;
+    l.ids = ids;
+    l.d2 = d2;
+    NSG_CK(nsg::launch_knn_direct(l, st));
+    return NSG_OK;
+}
+
+nsg_status navigate_run(const float *base, int64_t n, int d, const int *knn, int K, const double *c,
+                        int start, int L, int *nav_host, cudaStream_t st) {
+    DevBuf<uint32_t> visited;
+    DevBuf<int> out;
+    NSG_CK(visited.alloc((size_t)(n + 31) / 32));
+    NSG_CK(out.alloc(2));
+    NSG_CK(cudaMemsetAsync(visited.p, 0, sizeof(uint32_t) * ((n + 31) / 32), st));
+    NSG_CK(nsg::launch_navigate(base, n, d, knn, K, c, start, L, visited.p, default_steps(L), out.p,
+                                out.p + 1, st));
+    int h[2] = {0, 0};
+    NSG_CK(cudaMemcpyAsync(h, out.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    NSG_CK(cudaStreamSynchronize(st));
+    *nav_host = h[0];
+    return h[1] ? NSG_ESTEPCAP : NSG_OK;
+}
+
+nsg_status connect_run(const float *bp, int64_t n, int dp, int *adj, int *deg, int R, int nav, int L,
+                       int *n_added, cudaStream_t st) {
+    const int64_t nwords = (n + 31) / 32;
+    DevBuf<uint32_t> reached;
+    DevBuf<int> fa, fb, cnt, out;
+    NSG_CK(reached.alloc(nwords));
+    NSG_CK(fa.alloc(n));
+    NSG_CK(fb.alloc(n));
+    NSG_CK(cnt.alloc(2));
+    NSG_CK(out.alloc(4));
+    NSG_CK(cudaMemsetAsync(reached.p, 0, sizeof(uint32_t) * nwords, st));
+    NSG_CK(nsg::launch_bfs_seed(reached.p, nav, fa.p, cnt.p, st));
+    int nf = 1;
+    int *cur = fa.p, *nxt = fb.p;
+    for (int64_t level = 0; nf > 0 && level <= n; ++level) {
+        NSG_CK(cudaMemsetAsync(cnt.p + 1, 0, sizeof(int), st));
+        NSG_CK(nsg::launch_bfs_level(adj, R, cur, nf, nxt, cnt.p + 1, reached.p, st));
+        NSG_CK(cudaMemcpyAsync(&nf, cnt.p + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        NSG_CK(cudaStreamSynchronize(st));
+        std::swap(cur, nxt);
+    }
+    nsg::ConnectLaunch c;
+    c.base = bp;
+    c.n = n;
+    c.dp = dp;
+    c.adj = adj;
+    c.deg = deg;
+    c.R = R;
+    c.nav = nav;
+    c.L = L;
+    c.reached = reached.p;
+    c.queue = fa.p;
+    c.out = out.p;
+    c.hash_slots = default_hash(L, R);
+    c.max_steps = default_steps(L);
+    NSG_CK(cudaMemsetAsync(out.p, 0, 4 * sizeof(int), st));
+    NSG_CK(nsg::launch_connect(c, st));
+    int h[4] = {0, 0, 0, 0};
+    NSG_CK(cudaMemcpyAsync(h, out.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    NSG_CK(cudaStreamSynchronize(st));
+    if (n_added) *n_added = h[0];
+    if (h[1] == NSG_EDEGREE) return NSG_EDEGREE;
+    return h[2] ? NSG_ESTEPCAP : NSG_OK;
+}
+
+nsg_status collect_prune_all(const float *bp, int64_t n, int dp, const int *knn, int K, int nav, int L,
+                             int R, int C, int *adj, int *deg, float *ms_collect, float *ms_prune,
+                             cudaStream_t st) {
+    // candidate lists are materialised for a chunk of nodes at a time
+    const size_t budget = size_t(2) << 30;
+    int64_t chunk = (int64_t)(budget / ((size_t)C * 8 + 8));
+    if (chunk > n) chunk = n;
+    if (chunk < 1) chunk = 1;
+    DevBuf<int> cid, ccnt;
+    DevBuf<float> cd2;
+    NSG_CK(cid.alloc((size_t)chunk * C));
+    NSG_CK(cd2.alloc((size_t)chunk * C));
+    NSG_CK(ccnt.alloc(chunk));
+    cudaEvent_t ev[3];
+    for (auto &e : ev) NSG_CK(cudaEventCreate(&e));
+    float tc = 0, tp = 0;
+    nsg_status rc = NSG_OK;
+    for (int64_t v0 = 0; v0 < n && rc == NSG_OK; v0 += chunk) {
+        int64_t nv = n - v0 < chunk ? n - v0 : chunk;
+        nsg::CollectLaunch c;
+        c.base = bp;
+        c.n = n;
+        c.dp = dp;
+        c.knn = knn;
+        c.K = K;
+        c.nav = nav;
+        c.L = L;
+        c.C = C;
+        c.v0 = v0;
+        c.nv = nv;
+        c.hash_slots = default_hash(L, K);
+        c.max_steps = default_steps(L);
+        c.cand_ids = cid.p;
+        c.cand_d2 = cd2.p;
+        c.cand_count = ccnt.p;
+        c.status = nullptr;
+        cudaEventRecord(ev[0], st);
+        cudaError_t e = nsg::launch_collect(c, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "launch_collect");
+        cudaEventRecord(ev[1], st);
+        nsg::PruneLaunch p;
+        p.base = bp;
+        p.n = n;
+        p.dp = dp;
+        p.cand_ids = cid.p;
+        p.cand_d2 = cd2.p;
+        p.cand_count = ccnt.p;
+        p.C = C;
+        p.R = R;
+        p.v0 = v0;
+        p.nv = nv;
+        p.adj = adj;
+        p.deg = deg;
+        if (rc == NSG_OK) {
+            e = nsg::launch_prune(p, st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "launch_prune");
+        }
+        cudaEventRecord(ev[2], st);
+        e = cudaEventSynchronize(ev[2]);
+        if (e != cudaSuccess && rc == NSG_OK) rc = cuda_fail(e, "collect/prune");
+        float a = 0, b = 0;
+        cudaEventElapsedTime(&a, ev[0], ev[1]);
+        cudaEventElapsedTime(&b, ev[1], ev[2]);
+        tc += a;
+        tp += b;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (ms_collect) *ms_collect = tc;
+    if (ms_prune) *ms_prune = tp;
+    return rc;
+}
+
+nsg_status finish_index(nsg_index *ix, cudaStream_t st) {
+    std::vector<int> deg((size_t)ix->n);
+    NSG_CK(cudaMemcpyAsync(deg.data(), ix->deg, sizeof(int) * ix->n, cudaMemcpyDeviceToHost, st));
+    NSG_CK(cudaStreamSynchronize(st));
+    int64_t sum = 0;
+    int mx = 0;
+    for (int v : deg) {
+        sum += v;
+        mx = v > mx ? v : mx;
+    }
+    ix->max_degree = mx;
+    ix->avg_degree = ix->n ? (double)sum / (double)ix->n : 0.0;
+    NSG_CK(cudaMalloc(reinterpret_cast<void **>(&ix->flag), 4 * sizeof(int)));
+    return NSG_OK;
+}
+
+void destroy(nsg_index *ix) {
+    if (!ix) return;
+    if (ix->base) cudaFree(ix->base);
+    if (ix->adj) cudaFree(ix->adj);
+    if (ix->deg) cudaFree(ix->deg);
+    if (ix->flag) cudaFree(ix->flag);
+    delete ix;
+}
+
+double since_ms(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+namespace nsg {
+
+int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cache[dev]) cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev);
+    return cache[dev] > 0 ? cache[dev] : 1;
+}
+
+size_t smem_optin() {
+    static int cache[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cache[dev]) cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return cache[dev] > 0 ? (size_t)cache[dev] : 48 * 1024;
+}
+
+}  // namespace nsg
+
+extern "C" {
+
+const char *nsg_status_str(nsg_status s) {
+    switch (s) {
+    case NSG_OK: return "NSG_OK";
+    case NSG_EINVAL: return "NSG_EINVAL: invalid argument";
+    case NSG_ENOMEM: return "NSG_ENOMEM: allocation failed";
+    case NSG_ECUDA: return "NSG_ECUDA: CUDA runtime error";
+    case NSG_ESTEPCAP: return "NSG_ESTEPCAP: a search hit its step cap";
+    case NSG_EDEGREE: return "NSG_EDEGREE: no reached node has a free adjacency slot";
+    case NSG_EIO: return "NSG_EIO: file error";
+    case NSG_EFORMAT: return "NSG_EFORMAT: not an NSG index file";
+    }
+    return "unknown nsg_status";
+}
+
+const char *nsg_last_cuda_error(void) { return g_err; }
+
+nsg_status nsg_knn_init(const float *base_dev, int64_t n, int32_t d, int32_t K, int32_t *knn_ids_dev,
+                        float *knn_d2_dev, void *stream) {
+    if (!base_dev || !knn_ids_dev || n < 2 || d < 1 || d > 4 * nsg::MAX_DP4_HOST || K < 1 || K >= n ||
+        K > 256 || n >= INT32_MAX)
+        return NSG_EINVAL;
+    cudaStream_t st = S(stream);
+    DevBuf<float> tmp;
+    const float *bp = nullptr;
+    nsg_status s = padded_view(base_dev, n, d, tmp, &bp, st);
+    if (s) return s;
+    return knn_run(bp, n, round_up4(d), bp, n, 0, K, 1, knn_ids_dev, knn_d2_dev, st);
+}
+
+nsg_status nsg_knn_query(const float *base_dev, int64_t n, int32_t d, const float *queries_dev,
+                         int64_t nq, int32_t k, int32_t *ids_dev, float *d2_dev, void *stream) {
+    if (!base_dev || n < 1 || d < 1 || d > 4 * nsg::MAX_DP4_HOST || k < 1 || k > 256 || k > n ||
+        nq < 0 || n >= INT32_MAX)
+        return NSG_EINVAL;
+    if (nq == 0) return NSG_OK;
+    if (!queries_dev || !ids_dev) return NSG_EINVAL;
+    cudaStream_t st = S(stream);
+    DevBuf<float> tb, tq;
+    const float *bp = nullptr, *qp = nullptr;
+    nsg_status s = padded_view(base_dev, n, d, tb, &bp, st);
+    if (!s) s = padded_view(queries_dev, nq, d, tq, &qp, st);
+    if (s) return s;
+    return knn_run(bp, n, round_up4(d), qp, nq, 0, k, 0, ids_dev, d2_dev, st);
+}
+
+nsg_status nsg_centroid(const float *base_dev, int64_t n, int32_t d, double *centroid_dev, void *stream) {
+    if (!base_dev || !centroid_dev || n < 1 || d < 1) return NSG_EINVAL;
+    cudaStream_t st = S(stream);
+    int nb = nsg::sm_count() * 4;
+    DevBuf<double> part;
+    NSG_CK(part.alloc((size_t)nb * d));
+    NSG_CK(nsg::launch_centroid(base_dev, n, d, part.p, nb, centroid_dev, st));
+    NSG_CK(cudaStreamSynchronize(st));  // scratch is freed on return
+    return NSG_OK;
+}
+
+nsg_status nsg_navigate(const float *base_dev, int64_t n, int32_t d, const int32_t *knn_ids_dev,
+                        int32_t K, const double *centroid_dev, int32_t start, int32_t L,
+                        int32_t *nav_host, void *stream) {
+    if (!base_dev || !knn_ids_dev || !centroid_dev || !nav_host || n < 1 || d < 1 ||
+        d > 4 * nsg::MAX_DP4_HOST || K < 1 || L < 1 || L > 1024 || start < 0 || start >= n)
+        return NSG_EINVAL;
+    cudaStream_t st = S(stream);
+    nsg_status s = check_ids(knn_ids_dev, n * K, n, st);
+    if (s) return s;
+    return navigate_run(base_dev, n, d, knn_ids_dev, K, centroid_dev, start, L, nav_host, st);
+}
+
+nsg_status nsg_collect(const float *base_dev, int64_t n, int32_t d, const int32_t *knn_ids_dev,
+                       int32_t K, int32_t nav, int32_t L, int32_t C, int64_t v0, int64_t nv,
+                       int32_t *cand_ids_dev, float *cand_d2_dev, int32_t *cand_count_dev,
+                       int32_t *status_dev, void *stream) {
+    if (!base_dev || !knn_ids_dev || (d & 3) || !aligned16(base_dev) || d < 4 ||
+        d > 4 * nsg::MAX_DP4_HOST || n < 1 || K < 1 || K > 1024 || L < 1 || L > 1024 || C < 1 ||
+        C > 4096 || nav < 0 || nav >= n || v0 < 0 || nv < 0 || v0 + nv > n)
+        return NSG_EINVAL;
+    if (nv == 0) return NSG_OK;
+    if (!cand_ids_dev || !cand_d2_dev || !cand_count_dev) return NSG_EINVAL;
+    cudaStream_t st = S(stream);
+    nsg_status s = check_ids(knn_ids_dev, n * K, n, st);
+    if (s) return s;
+    nsg::CollectLaunch c;
+    c.base = base_dev;
+    c.n = n;
+    c.dp = d;
+    c.knn = knn_ids_dev;
+    c.K = K;
+    c.nav = nav;
+    c.L = L;
+    c.C = C;
+    c.v0 = v0;
+    c.nv = nv;
+    c.hash_slots = default_hash(L, K);
+    c.max_steps = default_steps(L);
+    c.cand_ids = cand_ids_dev;
+    c.cand_d2 = cand_d2_dev;
+    c.cand_count = cand_count_dev;
+    c.status = status_dev;
+    NSG_CK(nsg::launch_collect(c, st));
+    return NSG_OK;
+}
+
+nsg_status nsg_prune(const float *base_dev, int64_t n, int32_t d, const int32_t *cand_ids_dev,
+                     const float *cand_d2_dev, const int32_t *cand_count_dev, int32_t C, int32_t R,
+                     int64_t v0, int64_t nv, int32_t *adj_dev, int32_t *deg_dev, void *stream) {
+    if (!base_dev || (d & 3) || !aligned16(base_dev) || d < 4 || d > 4 * nsg::MAX_DP4_HOST || n < 1 ||
+        C < 1 || R < 1 || R > 1024 || v0 < 0 || nv < 0 || v0 + nv > n)
+        return NSG_EINVAL;
+    if (nv == 0) return NSG_OK;
+    if (!cand_ids_dev || !cand_d2_dev || !cand_count_dev || !adj_dev || !deg_dev) return NSG_EINVAL;
+    cudaStream_t st = S(stream);
+    nsg_status s = check_ids(cand_ids_dev, nv * C, n, st);
+    if (s) return s;
+    nsg::PruneLaunch p;
+    p.base = base_dev;
+    p.n = n;
+    p.dp = d;
+    p.cand_ids = cand_ids_dev;
+    p.cand_d2 = cand_d2_dev;
+    p.cand_count = cand_count_dev;
+    p.C = C;
+    p.R = R;
+    p.v0 = v0;
+    p.nv = nv;
+    p.adj = adj_dev;
+    p.deg = deg_dev;
+    NSG_CK(nsg::launch_prune(p, st));
+    return NSG_OK;
+}
+
+nsg_status nsg_connect(const float *base_dev, int64_t n, int32_t d, int32_t *adj_dev, int32_t *deg_dev,
+                       int32_t R, int32_t nav, int32_t L, int32_t *n_added_host, void *stream) {
+    if (!base_dev || !adj_dev || !deg_dev || (d & 3) || !aligned16(base_dev) || d < 4 ||
+        d > 4 * nsg::MAX_DP4_HOST || n < 1 || R < 1 || R > 1024 || L < 1 || L > 1024 || nav < 0 ||
+        nav >= n)
+        return NSG_EINVAL;
+    cudaStream_t st = S(stream);
+    nsg_status s = check_ids(adj_dev, n * R, n, st);
+    if (s) return s;
+    return connect_run(base_dev, n, d, adj_dev, deg_dev, R, nav, L, n_added_host, st);
+}
+
+nsg_status nsg_build(const float *base_dev, int64_t n, int32_t d, int32_t K, int32_t L, int32_t R,
+                     int32_t C, uint64_t seed, void *stream, nsg_index **out) {
+    if (!out) return NSG_EINVAL;
+    *out = nullptr;
+    if (!base_dev || n < 2 || n >= INT32_MAX || d < 1 || d > 4 * nsg::MAX_DP4_HOST || K < 1 || K >= n ||
+        K > 256 || L < 1 || L > 1024 || R < 1 || R > 1024 || C < R || C > 4096)
+        return NSG_EINVAL;
+    cudaStream_t st = S(stream);
+    auto t_all = std::chrono::steady_clock::now();
+    nsg_index *ix = new (std::nothrow) nsg_index;
+    if (!ix) return NSG_ENOMEM;
+    ix->n = n;
+    ix->d = d;
+    ix->dp = round_up4(d);
+    ix->R = R;
+    DevBuf<float> base;
+    DevBuf<int> adj, deg, knn;
+    DevBuf<double> cen, part;
+    nsg_status s = padded_copy(base_dev, n, d, ix->dp, base, st);
+    cudaError_t e = cudaSuccess;
+    if (!s && (e = adj.alloc((size_t)n * R)) != cudaSuccess) s = cuda_fail(e, "alloc adj");
+    if (!s && (e = deg.alloc((size_t)n)) != cudaSuccess) s = cuda_fail(e, "alloc deg");
+    if (!s && (e = knn.alloc((size_t)n * K)) != cudaSuccess) s = cuda_fail(e, "alloc knn");
+    // A1: kNN graph
+    auto t0 = std::chrono::steady_clock::now();
+    if (!s) s = knn_run(base.p, n, ix->dp, base.p, n, 0, K, 1, knn.p, nullptr, st);
+    if (!s && (e = cudaStreamSynchronize(st)) != cudaSuccess) s = cuda_fail(e, "knn");
+    ix->ms[0] = (float)since_ms(t0);
+    // A2 + A3: centroid and navigating node
+    t0 = std::chrono::steady_clock::now();
+    int nb = nsg::sm_count() * 4;
+    if (!s && (e = part.alloc((size_t)nb * ix->dp)) != cudaSuccess) s = cuda_fail(e, "alloc part");
+    if (!s && (e = cen.alloc((size_t)ix->dp)) != cudaSuccess) s = cuda_fail(e, "alloc centroid");
+    if (!s && (e = nsg::launch_centroid(base.p, n, ix->dp, part.p, nb, cen.p, st)) != cudaSuccess)
+        s = cuda_fail(e, "centroid");
+    const int start = (int)(splitmix64(seed) % (uint64_t)n);
+    if (!s) s = navigate_run(base.p, n, ix->dp, knn.p, K, cen.p, start, L, &ix->nav, st);
+    ix->ms[1] = (float)since_ms(t0);
+    // A5 + A6: search-collect-select per node
+    if (!s)
+        s = collect_prune_all(base.p, n, ix->dp, knn.p, K, ix->nav, L, R, C, adj.p, deg.p, &ix->ms[2],
+                              &ix->ms[3], st);
+    knn.alloc(0);  // release the kNN graph before the connectivity pass
+    // A7: connectivity
+    t0 = std::chrono::steady_clock::now();
+    int added = 0;
+    if (!s) s = connect_run(base.p, n, ix->dp, adj.p, deg.p, R, ix->nav, L, &added, st);
+    ix->ms[4] = (float)since_ms(t0);
+    ix->n_fixup = added;
+    if (s) {
+        destroy(ix);
+        return s;
+    }
+    ix->base = base.release();
+    ix->adj = adj.release();
+    ix->deg = deg.release();
+    s = finish_index(ix, st);
+    ix->ms[5] = (float)since_ms(t_all);
+    if (s) {
+        destroy(ix);
+        return s;
+    }
+    *out = ix;
+    return NSG_OK;
+}
+
+nsg_status nsg_index_from_graph(const float *base_dev, int64_t n, int32_t d, const int32_t *adj_dev,
+                                const int32_t *deg_dev, int32_t R, int32_t nav, void *stream,
+                                nsg_index **out) {
+    if (!out) return NSG_EINVAL;
+    *out = nullptr;
+    if (!base_dev || !adj_dev || n < 1 || n >= INT32_MAX || d < 1 || d > 4 * nsg::MAX_DP4_HOST ||
+        R < 1 || R > 1024 || nav < 0 || nav >= n)
+        return NSG_EINVAL;
+    cudaStream_t st = S(stream);
+    nsg_status s = check_ids(adj_dev, n * R, n, st);
+    if (s) return s;
+    nsg_index *ix = new (std::nothrow) nsg_index;
+    if (!ix) return NSG_ENOMEM;
+    ix->n = n;
+    ix->d = d;
+    ix->dp = round_up4(d);
+    ix->R = R;
+    ix->nav = nav;
+    DevBuf<float> base;
+    DevBuf<int> adj, deg;
+    s = padded_copy(base_dev, n, d, ix->dp, base, st);
+    cudaError_t e = cudaSuccess;
+    if (!s && (e = adj.alloc((size_t)n * R)) != cudaSuccess) s = cuda_fail(e, "alloc adj");
+    if (!s && (e = deg.alloc((size_t)n)) != cudaSuccess) s = cuda_fail(e, "alloc deg");
+    if (!s && (e = cudaMemcpyAsync(adj.p, adj_dev, sizeof(int) * n * R, cudaMemcpyDeviceToDevice, st)) !=
+                  cudaSuccess)
+        s = cuda_fail(e, "copy adj");
+    if (!s) {
+        if (deg_dev) {
+            e = cudaMemcpyAsync(deg.p, deg_dev, sizeof(int) * n, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) s = cuda_fail(e, "copy deg");
+        } else {
+            std::vector<int> h((size_t)n * R), dg((size_t)n);
+            e = cudaMemcpyAsync(h.data(), adj_dev, sizeof(int) * n * R, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess) {
+                for (int64_t v = 0; v < n; ++v) {
+                    int c = 0;
+                    while (c < R && h[v * R + c] >= 0) ++c;
+                    dg[v] = c;
+                }
+                e = cudaMemcpyAsync(deg.p, dg.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            }
+            if (e != cudaSuccess) s = cuda_fail(e, "degrees");
+        }
+    }
+    if (s) {
+        destroy(ix);
+        return s;
+    }
+    ix->base = base.release();
+    ix->adj = adj.release();
+    ix->deg = deg.release();
+    s = finish_index(ix, st);
+    if (s) {
+        destroy(ix);
+        return s;
+    }
+    *out = ix;
+    return NSG_OK;
+}
+
+nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k,
+                         int32_t L, const nsg_search_params *params, int32_t *ids_dev, float *d2_dev,
+                         int32_t *n_expand_dev, int32_t *n_dist_dev, int32_t *status_dev, void *stream) {
+    if (!idx || k < 1 || L < k || L > 1024 || nq < 0 || nq >= INT32_MAX) return NSG_EINVAL;
+    if (nq == 0) return NSG_OK;
+    if (!queries_dev || !ids_dev) return NSG_EINVAL;
+    nsg_search_params p = {0, 0, NSG_PREC_F32, 0};
+    if (params) p = *params;
+    if (p.precision != NSG_PREC_F32) return NSG_EINVAL;
+    if (p.hash_slots > 0 && (p.hash_slots < 64 || (p.hash_slots & (p.hash_slots - 1)) || p.hash_slots > 65536))
+        return NSG_EINVAL;
+    nsg::SearchLaunch l;
+    l.base = idx->base;
+    l.n = idx->n;
+    l.dp = idx->dp;
+    l.adj = idx->adj;
+    l.width = idx->R;
+    l.start = idx->nav;
+    l.queries = queries_dev;
+    l.d = idx->d;
+    l.nq = nq;
+    l.k = k;
+    l.L = L;
+    l.hash_slots = p.hash_slots > 0 ? p.hash_slots : default_hash(L, idx->R);
+    l.max_steps = p.max_steps > 0 ? p.max_steps : default_steps(L);
+    l.warps_per_cta = p.warps_per_cta;
+    l.ids = ids_dev;
+    l.d2 = d2_dev;
+    l.n_expand = n_expand_dev;
+    l.n_dist = n_dist_dev;
+    l.status = status_dev;
+    l.any_capped = nullptr;
+    NSG_CK(nsg::launch_search(l, S(stream)));
+    return NSG_OK;
+}
+
+nsg_status nsg_search(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k, int32_t L,
+                      int32_t *ids_dev, float *d2_dev, void *stream) {
+    if (!idx || k < 1 || L < k || L > 1024 || nq < 0 || nq >= INT32_MAX) return NSG_EINVAL;
+    if (nq == 0) return NSG_OK;
+    if (!queries_dev || !ids_dev) return NSG_EINVAL;
+    cudaStream_t st = S(stream);
+    nsg::SearchLaunch l;
+    l.base = idx->base;
+    l.n = idx->n;
+    l.dp = idx->dp;
+    l.adj = idx->adj;
+    l.width = idx->R;
+    l.start = idx->nav;
+    l.queries = queries_dev;
+    l.d = idx->d;
+    l.nq = nq;
+    l.k = k;
+    l.L = L;
+    l.hash_slots = default_hash(L, idx->R);
+    l.max_steps = default_steps(L);
+    l.warps_per_cta = 0;
+    l.ids = ids_dev;
+    l.d2 = d2_dev;
+    l.n_expand = nullptr;
+    l.n_dist = nullptr;
+    l.status = nullptr;
+    l.any_capped = idx->flag;
+    NSG_CK(cudaMemsetAsync(idx->flag, 0, sizeof(int), st));
+    NSG_CK(nsg::launch_search(l, st));
+    int h = 0;
+    NSG_CK(cudaMemcpyAsync(&h, idx->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NSG_CK(cudaStreamSynchronize(st));
+    return h ? NSG_ESTEPCAP : NSG_OK;
+}
+
+nsg_status nsg_recall(const int32_t *ids_dev, int32_t ld_ids, const int32_t *gt_dev, int32_t ld_gt,
+                      int64_t nq, int32_t k, int32_t *hits_dev, void *stream) {
+    if (nq < 0 || k < 1 || ld_ids < k || ld_gt < k) return NSG_EINVAL;
+    if (nq == 0) return NSG_OK;
+    if (!ids_dev || !gt_dev || !hits_dev) return NSG_EINVAL;
+    NSG_CK(nsg::launch_recall(ids_dev, ld_ids, gt_dev, ld_gt, nq, k, hits_dev, S(stream)));
+    return NSG_OK;
+}
+
+nsg_status nsg_index_info(const nsg_index *idx, nsg_index_info_t *info) {
+    if (!idx || !info) return NSG_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    info->n = idx->n;
+    info->d = idx->d;
+    info->R = idx->R;
+    info->nav = idx->nav;
+    info->max_degree = idx->max_degree;
+    info->avg_degree = idx->avg_degree;
+    info->n_fixup_edges = idx->n_fixup;
+    info->device_bytes = (int64_t)idx->n * idx->dp * 4 + (int64_t)idx->n * idx->R * 4 + idx->n * 4 + 16;
+    info->ms_knn = idx->ms[0];
+    info->ms_centroid_nav = idx->ms[1];
+    info->ms_collect = idx->ms[2];
+    info->ms_prune = idx->ms[3];
+    info->ms_connect = idx->ms[4];
+    info->ms_total = idx->ms[5];
+    return NSG_OK;
+}
+
+nsg_status nsg_index_graph(const nsg_index *idx, int32_t *adj_dev, int32_t *deg_dev, void *stream) {
+    if (!idx) return NSG_EINVAL;
+    cudaStream_t st = S(stream);
+    if (adj_dev)
+        NSG_CK(cudaMemcpyAsync(adj_dev, idx->adj, sizeof(int) * idx->n * idx->R, cudaMemcpyDeviceToDevice, st));
+    if (deg_dev) NSG_CK(cudaMemcpyAsync(deg_dev, idx->deg, sizeof(int) * idx->n, cudaMemcpyDeviceToDevice, st));
+    return NSG_OK;
+}
+
+static const char kMagic[8] = {'N', 'S', 'G', 'G', 'B', '3', '0', '0'};
+
+nsg_status nsg_save(const nsg_index *idx, const char *path) {
+    if (!idx || !path) return NSG_EINVAL;
+    const int64_t n = idx->n;
+    std::vector<int> deg((size_t)n), adj((size_t)n * idx->R);
+    std::vector<float> base((size_t)n * idx->d);
+    NSG_CK(cudaMemcpy(deg.data(), idx->deg, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    NSG_CK(cudaMemcpy(adj.data(), idx->adj, sizeof(int) * n * idx->R, cudaMemcpyDeviceToHost));
+    NSG_CK(cudaMemcpy2D(base.data(), sizeof(float) * idx->d, idx->base, sizeof(float) * idx->dp,
+                        sizeof(float) * idx->d, n, cudaMemcpyDeviceToHost));
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return NSG_EIO;
+    int32_t hdr[4] = {1, idx->d, idx->R, idx->nav};
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, 4, 1, f) == 1 &&
+              std::fwrite(&n, 8, 1, f) == 1 && std::fwrite(&hdr[1], 4, 3, f) == 3 &&
+              std::fwrite(deg.data(), 4, deg.size(), f) == deg.size() &&
+              std::fwrite(adj.data(), 4, adj.size(), f) == adj.size() &&
+              std::fwrite(base.data(), 4, base.size(), f) == base.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? NSG_OK : NSG_EIO;
+}
+
+nsg_status nsg_load(const char *path, void *stream, nsg_index **out) {
+    if (!path || !out) return NSG_EINVAL;
+    *out = nullptr;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return NSG_EIO;
+    char magic[8];
+    int32_t ver = 0, hdr[3] = {0, 0, 0};
+    int64_t n = 0;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::fread(&ver, 4, 1, f) == 1 &&
+              std::fread(&n, 8, 1, f) == 1 && std::fread(hdr, 4, 3, f) == 3;
+    if (!ok || std::memcmp(magic, kMagic, 8) != 0 || ver != 1 || n < 1 || n >= INT32_MAX || hdr[0] < 1 ||
+        hdr[0] > 4 * nsg::MAX_DP4_HOST || hdr[1] < 1 || hdr[1] > 1024 || hdr[2] < 0 || hdr[2] >= n) {
+        std::fclose(f);
+        return ok ? NSG_EFORMAT : NSG_EIO;
+    }
+    const int d = hdr[0], R = hdr[1], nav = hdr[2];
+    std::vector<int> deg((size_t)n), adj((size_t)n * R);
+    std::vector<float> base((size_t)n * d);
+    ok = std::fread(deg.data(), 4, deg.size(), f) == deg.size() &&
+         std::fread(adj.data(), 4, adj.size(), f) == adj.size() &&
+         std::fread(base.data(), 4, base.size(), f) == base.size();
+    std::fclose(f);
+    if (!ok) return NSG_EFORMAT;
+    for (int64_t v = 0; v < n; ++v) {
+        if (deg[v] < 0 || deg[v] > R) return NSG_EFORMAT;
+        for (int t = 0; t < R; ++t) {
+            int x = adj[v * R + t];
+            if (x < -1 || x >= n) return NSG_EFORMAT;
+        }
+    }
+    cudaStream_t st = S(stream);
+    DevBuf<float> db;
+    DevBuf<int> da, dd;
+    NSG_CK(db.alloc(base.size()));
+    NSG_CK(da.alloc(adj.size()));
+    NSG_CK(dd.alloc(deg.size()));
+    NSG_CK(cudaMemcpyAsync(db.p, base.data(), 4 * base.size(), cudaMemcpyHostToDevice, st));
+    NSG_CK(cudaMemcpyAsync(da.p, adj.data(), 4 * adj.size(), cudaMemcpyHostToDevice, st));
+    NSG_CK(cudaMemcpyAsync(dd.p, deg.data(), 4 * deg.size(), cudaMemcpyHostToDevice, st));
+    NSG_CK(cudaStreamSynchronize(st));
+    return nsg_index_from_graph(db.p, n, d, da.p, dd.p, R, nav, stream, out);
+}
+
+void nsg_free(nsg_index *idx) { destroy(idx); }
+
+}  // extern "C"

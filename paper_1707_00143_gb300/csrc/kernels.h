@@ -1,0 +1,116 @@
+// kernels.h -- host-side launchers of the NSG kernels (internal to libnsg).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nsg {
+
+constexpr int MAX_DP4_HOST = 512;  // largest supported row: 2048 floats
+
+// Search on a fixed-width graph (Alg. 1 from `start`), one warp per query.
+struct SearchLaunch {
+    const float *base;  // [n][dp] padded, 16-byte aligned
+    int64_t n;
+    int dp;
+    const int *adj;  // [n][width]
+    int width;
+    int start;
+    const float *queries;  // [nq][d]
+    int d;
+    int64_t nq;
+    int k, L;
+    int hash_slots, max_steps, warps_per_cta;
+    int *ids;
+    float *d2;
+    int *n_expand, *n_dist, *status;
+    int *any_capped;  // device flag, nullable
+};
+cudaError_t launch_search(const SearchLaunch &a, cudaStream_t st);
+
+// Search-and-collect on the kNN graph for nodes v0..v0+nv-1.
+struct CollectLaunch {
+    const float *base;  // [n][dp]
+    int64_t n;
+    int dp;
+    const int *knn;  // [n][K]
+    int K, nav, L, C;
+    int64_t v0, nv;
+    int hash_slots, max_steps;
+    int *cand_ids;
+    float *cand_d2;
+    int *cand_count;
+    int *status;
+};
+cudaError_t launch_collect(const CollectLaunch &a, cudaStream_t st);
+
+// MRNG edge selection for nodes v0..v0+nv-1.
+struct PruneLaunch {
+    const float *base;  // [n][dp]
+    int64_t n;
+    int dp;
+    const int *cand_ids;
+    const float *cand_d2;
+    const int *cand_count;
+    int C, R;
+    int64_t v0, nv;
+    int *adj;
+    int *deg;
+};
+cudaError_t launch_prune(const PruneLaunch &a, cudaStream_t st);
+
+// Centroid in FP64: partial sums per block then an ordered final sum.
+cudaError_t launch_centroid(const float *base, int64_t n, int d, double *partial, int nblocks,
+                            double *c, cudaStream_t st);
+
+// Navigating node search (single warp, FP64 distances to the centroid).
+cudaError_t launch_navigate(const float *base, int64_t n, int d, const int *knn, int K,
+                            const double *c, int start, int L, uint32_t *visited_bits,
+                            int max_steps, int *nav_out, int *status, cudaStream_t st);
+
+// BFS helpers and the connectivity pass.
+cudaError_t launch_bfs_seed(uint32_t *reached, int root, int *frontier, int *count, cudaStream_t st);
+cudaError_t launch_bfs_level(const int *adj, int R, const int *frontier, int nf, int *next,
+                             int *next_count, uint32_t *reached, cudaStream_t st);
+struct ConnectLaunch {
+    const float *base;  // [n][dp]
+    int64_t n;
+    int dp;
+    int *adj;  // [n][R]
+    int *deg;
+    int R, nav, L;
+    uint32_t *reached;  // n bits, reach from nav already marked
+    int *queue;         // [n]
+    int *out;           // [0]=edges added, [1]=status, [2]=steps capped
+    int hash_slots, max_steps;
+};
+cudaError_t launch_connect(const ConnectLaunch &a, cudaStream_t st);
+
+// Precision hits per query (Eq. 1).
+cudaError_t launch_recall(const int *ids, int ld_ids, const int *gt, int ld_gt, int64_t nq, int k,
+                          int *hits, cudaStream_t st);
+
+// Exact FP32 brute-force k nearest neighbours (serial scan on CUDA cores).
+// self_join: queries are the base rows q0.. and each row's own id is skipped.
+struct KnnLaunch {
+    const float *base;  // [n][dp]
+    int64_t n;
+    int dp;
+    const float *queries;  // [nq][dp]
+    int64_t nq;
+    int64_t q0;  // id of query 0 when self_join
+    int k;
+    int self_join;
+    int *ids;
+    float *d2;
+};
+cudaError_t launch_knn_direct(const KnnLaunch &a, cudaStream_t st);
+
+// Padding copy [n][d] -> [n][dp] (zeros in the pad).
+cudaError_t launch_pad_rows(const float *src, int64_t n, int d, float *dst, int dp, cudaStream_t st);
+
+// Device properties cached per device.
+int sm_count();
+size_t smem_optin();
+
+}  // namespace nsg

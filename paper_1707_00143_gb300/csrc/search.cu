@@ -1,0 +1,212 @@
+// search.cu -- Alg. 1 for a batch of queries (search on NSG, Section 3.5) and
+// the per-node search-and-collect of Alg. 2 (lines 5-8), one warp per unit.
+#include <algorithm>
+
+#include "kernels.h"
+#include "search_core.cuh"
+
+namespace nsg {
+
+__host__ __device__ static inline int round32(int x) { return (x + 31) & ~31; }
+static inline int log2i(unsigned x) {
+    int r = 0;
+    while ((1u << r) < x) ++r;
+    return r;
+}
+
+struct SearchArgs {
+    const float4 *base4;
+    int dp4;
+    const int *adj;
+    int width, W;
+    int start;
+    const float *queries;
+    int d;
+    int64_t nq;
+    int k, L, H, hshift, max_steps;
+    int *ids;
+    float *d2;
+    int *n_expand, *n_dist, *status, *any_capped;
+};
+
+template <int G, int V, int U>
+__global__ void __launch_bounds__(256) search_kernel(SearchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const unsigned lane = lane_id();
+    WarpSmem s = carve_warp_smem(smem + warp * warp_smem_bytes(a.L, a.W, 0, a.H), a.L, a.W, 0, a.H);
+    int csize = 0;
+    const int64_t stride = (int64_t)gridDim.x * wpb;
+    for (int64_t qi = (int64_t)blockIdx.x * wpb + warp; qi < a.nq; qi += stride) {
+        RowQuery<G, V> Q;
+        Q.load(a.queries + qi * a.d, a.d, a.dp4);
+        SearchOut o = warp_alg1<G, V, U, false, false>(Q, a.base4, a.dp4, GraphRef{a.adj, a.width},
+                                                        a.start, a.L, s, (uint32_t)a.H - 1, a.hshift,
+                                                        a.max_steps, -1, 0, csize);
+        for (int t = lane; t < a.k; t += 32) {
+            uint64_t e = t < o.size ? s.pool[t] : KEY_INF;
+            a.ids[qi * a.k + t] = t < o.size ? kid(e) : -1;
+            if (a.d2) a.d2[qi * a.k + t] = t < o.size ? kd2(e) : __int_as_float(0x7f800000);
+        }
+        if (lane == 0) {
+            if (a.n_expand) a.n_expand[qi] = o.n_expand;
+            if (a.n_dist) a.n_dist[qi] = o.n_dist;
+            if (a.status) a.status[qi] = o.capped ? -4 : 0;
+            if (o.capped && a.any_capped) atomicOr(a.any_capped, 1);
+        }
+        __syncwarp();
+    }
+}
+
+struct CollectArgs {
+    const float4 *base4;
+    int dp4;
+    const int *knn;
+    int K, W, nav, L, C, H, hshift, max_steps;
+    int64_t v0, nv;
+    int *cand_ids;
+    float *cand_d2;
+    int *cand_count, *status;
+};
+
+template <int G, int V, int U>
+__global__ void __launch_bounds__(256) collect_kernel(CollectArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const unsigned lane = lane_id();
+    WarpSmem s = carve_warp_smem(smem + warp * warp_smem_bytes(a.L, a.W, a.C, a.H), a.L, a.W, a.C, a.H);
+    const int64_t stride = (int64_t)gridDim.x * wpb;
+    const uint32_t hmask = (uint32_t)a.H - 1;
+    for (int64_t j = (int64_t)blockIdx.x * wpb + warp; j < a.nv; j += stride) {
+        const int v = (int)(a.v0 + j);
+        RowQuery<G, V> Q;
+        Q.load_row(a.base4 + (int64_t)v * a.dp4, a.dp4);
+        int csize = 0;
+        SearchOut o = warp_alg1<G, V, U, true, false>(Q, a.base4, a.dp4, GraphRef{a.knn, a.K}, a.nav,
+                                                       a.L, s, hmask, a.hshift, a.max_steps, v, a.C,
+                                                       csize);
+        // Alg. 2 line 7: v's nearest neighbours in G join the candidates
+        const int *row = a.knn + (int64_t)v * a.K;
+        int m = 0;
+        for (int b = 0; b < a.K; b += 32) {
+            int slot = b + (int)lane;
+            int w = slot < a.K ? __ldg(row + slot) : -1;
+            bool fresh = w >= 0 && visit(s.hash, hmask, a.hshift, w);
+            unsigned bal = __ballot_sync(NSG_FULL, fresh);
+            if (fresh) s.ids[m + __popc(bal & lanemask_lt())] = w;
+            m += __popc(bal);
+        }
+        __syncwarp();
+        if (m > 0) {
+            rows_dist<G, V, U>(Q, a.base4, a.dp4, s.ids, m, s.keys);
+            collect_merge(s, m, v, a.C, csize);
+        }
+        // Alg. 2 line 8: sorted candidates, cut to C
+        for (int t = lane; t < a.C; t += 32) {
+            uint64_t e = t < csize ? s.clist[t] : KEY_INF;
+            a.cand_ids[j * a.C + t] = t < csize ? kid(e) : -1;
+            a.cand_d2[j * a.C + t] = t < csize ? kd2(e) : __int_as_float(0x7f800000);
+        }
+        if (lane == 0) {
+            a.cand_count[j] = csize;
+            if (a.status) a.status[j] = o.capped ? -4 : 0;
+        }
+        __syncwarp();
+    }
+}
+
+template <typename K>
+static cudaError_t config(K kernel, size_t smem_per_warp, int want_wpb, int64_t units, int *grid,
+                          int *wpb, size_t *smem) {
+    size_t cap = smem_optin();
+    int w = want_wpb > 0 ? want_wpb : 4;
+    while (w > 1 && smem_per_warp * w > cap) --w;
+    if (smem_per_warp * w > cap) return cudaErrorInvalidConfiguration;
+    *smem = smem_per_warp * w;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, w * 32, *smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int64_t need = (units + w - 1) / w;
+    int64_t full = (int64_t)sm_count() * per_sm;
+    *grid = (int)std::max<int64_t>(1, std::min(need, full));
+    *wpb = w;
+    return cudaSuccess;
+}
+
+cudaError_t launch_search(const SearchLaunch &l, cudaStream_t st) {
+    if (l.nq <= 0) return cudaSuccess;
+    SearchArgs a;
+    a.base4 = reinterpret_cast<const float4 *>(l.base);
+    a.dp4 = l.dp / 4;
+    a.adj = l.adj;
+    a.width = l.width;
+    a.W = round32(l.width);
+    a.start = l.start;
+    a.queries = l.queries;
+    a.d = l.d;
+    a.nq = l.nq;
+    a.k = l.k;
+    a.L = l.L;
+    a.H = l.hash_slots;
+    a.hshift = 32 - log2i((unsigned)l.hash_slots);
+    a.max_steps = l.max_steps;
+    a.ids = l.ids;
+    a.d2 = l.d2;
+    a.n_expand = l.n_expand;
+    a.n_dist = l.n_dist;
+    a.status = l.status;
+    a.any_capped = l.any_capped;
+    size_t per_warp = warp_smem_bytes(a.L, a.W, 0, a.H);
+    cudaError_t err = cudaSuccess;
+    NSG_DISPATCH_DP4(a.dp4, {
+        auto kern = search_kernel<G_, V_, U_>;
+        int grid, wpb;
+        size_t smem;
+        err = config(kern, per_warp, l.warps_per_cta, l.nq, &grid, &wpb, &smem);
+        if (err == cudaSuccess) {
+            kern<<<grid, wpb * 32, smem, st>>>(a);
+            err = cudaGetLastError();
+        }
+    });
+    return err;
+}
+
+cudaError_t launch_collect(const CollectLaunch &l, cudaStream_t st) {
+    if (l.nv <= 0) return cudaSuccess;
+    CollectArgs a;
+    a.base4 = reinterpret_cast<const float4 *>(l.base);
+    a.dp4 = l.dp / 4;
+    a.knn = l.knn;
+    a.K = l.K;
+    a.W = round32(l.K);
+    a.nav = l.nav;
+    a.L = l.L;
+    a.C = l.C;
+    a.H = l.hash_slots;
+    a.hshift = 32 - log2i((unsigned)l.hash_slots);
+    a.max_steps = l.max_steps;
+    a.v0 = l.v0;
+    a.nv = l.nv;
+    a.cand_ids = l.cand_ids;
+    a.cand_d2 = l.cand_d2;
+    a.cand_count = l.cand_count;
+    a.status = l.status;
+    size_t per_warp = warp_smem_bytes(a.L, a.W, a.C, a.H);
+    cudaError_t err = cudaSuccess;
+    NSG_DISPATCH_DP4(a.dp4, {
+        auto kern = collect_kernel<G_, V_, U_>;
+        int grid, wpb;
+        size_t smem;
+        err = config(kern, per_warp, 4, l.nv, &grid, &wpb, &smem);
+        if (err == cudaSuccess) {
+            kern<<<grid, wpb * 32, smem, st>>>(a);
+            err = cudaGetLastError();
+        }
+    });
+    return err;
+}
+
+}  // namespace nsg

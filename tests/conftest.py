@@ -21,3 +21,21 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return GOLDEN
+
+
+def pytest_runtest_setup(item):
+    if item.get_closest_marker("gpu") is not None:
+        import torch
+
+        if not torch.cuda.is_available():
+            pytest.fail("GPU test selected but no CUDA device is visible", pytrace=False)
+
+
+@pytest.fixture(scope="session")
+def nsg():
+    """The CUDA library, built in-tree for sm_103a (fails loudly if it cannot be)."""
+    from paper_1707_00143_gb300 import build, capi
+
+    build.build()
+    capi.lib()
+    return capi
