@@ -106,6 +106,11 @@ struct KnnLaunch {
 };
 cudaError_t launch_knn_direct(const KnnLaunch &a, cudaStream_t st);
 
+// Tensor-core kNN (BF16 GEMM + fused top-k) when the data allows an exact
+// answer (integer values 0..255, d <= 128, k <= 256): *used = 1 when it ran,
+// 0 when it does not apply (nothing written).  Synchronises the stream.
+cudaError_t launch_knn_tc(const KnnLaunch &a, int *used, cudaStream_t st);
+
 // Padding copy [n][d] -> [n][dp] (zeros in the pad).
 cudaError_t launch_pad_rows(const float *src, int64_t n, int d, float *dst, int dp, cudaStream_t st);
 

@@ -1,0 +1,82 @@
+"""Brute-force kNN on the GPU (serial scan, Section 4.1.2) against the oracle.
+
+Integer data in 0..255 with d <= 128 takes the tensor-core path (BF16 GEMM,
+FP32 accumulation, fused top-k): distances are exact integers there, so ids
+and distances must equal the oracle bit for bit.  Other data takes the exact
+FP32 CUDA-core scan; its distances differ from the oracle's only by summation
+order (relative 1e-5, the tolerance stated for float data)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1707_00143_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def H(t):
+    return t.cpu().numpy()
+
+
+@pytest.fixture
+def scan_engine():
+    os.environ["NSG_KNN_ENGINE"] = "scan"
+    yield
+    os.environ.pop("NSG_KNN_ENGINE", None)
+
+
+@pytest.mark.parametrize("n,d,k,hi", [(1000, 32, 10, 256), (777, 128, 100, 256), (2000, 96, 256, 256),
+                                      (1300, 64, 17, 3), (300, 128, 1, 256)])
+def test_knn_init_tensor_core_bit_exact(nsg, n, d, k, hi):
+    # ragged row blocks (n % 128 != 0), K padding (d = 96 -> 128), ties (hi = 3)
+    base = datagen.uniform_int(n, d, seed=n + d, hi=hi)
+    ids, d2 = nsg.nsg_knn_init(T(base), k)
+    rid, rd2 = oracle.knn_rows(base, k)
+    assert np.array_equal(H(d2), rd2)
+    assert np.array_equal(H(ids), rid)
+
+
+@pytest.mark.parametrize("nq,k", [(1, 10), (129, 100), (300, 256)])
+def test_knn_query_tensor_core_bit_exact(nsg, nq, k):
+    base, q = datagen.workload("tiny", n=5000, nq=nq)
+    ids, d2 = nsg.nsg_knn_query(T(base), T(q), k)
+    rid, rd2 = oracle.knn_query(base, q, k)
+    assert np.array_equal(H(d2), rd2)
+    assert np.array_equal(H(ids), rid)
+
+
+def test_tensor_core_equals_scan_engine(nsg, scan_engine):
+    base = datagen.duplicate_rows(datagen.uniform_int(3000, 128, seed=61, hi=8), 200, seed=62)
+    a_ids, a_d2 = nsg.nsg_knn_init(T(base), 50)  # scan (fixture sets the engine)
+    os.environ.pop("NSG_KNN_ENGINE")
+    b_ids, b_d2 = nsg.nsg_knn_init(T(base), 50)  # tensor cores
+    assert torch.equal(a_ids, b_ids) and torch.equal(a_d2, b_d2)
+
+
+def test_float_data_uses_exact_scan_within_tolerance(nsg):
+    base = datagen.uniform_float(2500, 40, seed=63)
+    q = datagen.uniform_float(70, 40, seed=64)
+    ids, d2 = nsg.nsg_knn_query(T(base), T(q), 20)
+    rid, rd2 = oracle.knn_query(base, q, 20)
+    ids, d2 = H(ids), H(d2)
+    assert np.allclose(d2, rd2, rtol=1e-5, atol=0)
+    # ids agree except where two candidates are within rounding of each other
+    same = (ids == rid).mean()
+    assert same > 0.99
+    exact = ((base[ids].astype(np.float64) - q[:, None, :]) ** 2).sum(-1)
+    assert np.allclose(d2, exact, rtol=1e-5, atol=0)
+
+
+def test_knn_large_d_uses_scan_bit_exact(nsg):
+    # d = 200 > 128: the CUDA-core scan; integer data is still exact in any order
+    base = datagen.uniform_int(900, 200, seed=65)
+    ids, d2 = nsg.nsg_knn_init(T(base), 30)
+    rid, rd2 = oracle.knn_rows(base, 30)
+    assert np.array_equal(H(ids), rid) and np.array_equal(H(d2), rd2)
