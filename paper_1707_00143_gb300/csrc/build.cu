@@ -1,7 +1,7 @@
 // build.cu -- Alg. 2 kernels other than the per-node search: centroid (line 1),
 // navigating node (lines 2-3), MRNG edge selection (lines 9-20), reachability
-// and the connectivity pass (lines 21-28); plus the precision count (Eq. 1)
-// and a row-padding copy.
+// BFS helpers of the connectivity pass (lines 21-28, see connect.cu); plus the
+// precision count (Eq. 1) and a row-padding copy.
 #include <climits>
 
 #include "kernels.h"
@@ -304,157 +304,6 @@ cudaError_t launch_bfs_level(const int *adj, int R, const int *frontier, int nf,
     bfs_level_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, st>>>(adj, R, frontier, nf, next,
                                                                          next_count, reached);
     return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Connectivity pass (Alg. 2 lines 21-28), one CTA of 8 warps that loops
-// until every node is reached: smallest unreached id u -> warp 0 runs Alg. 1
-// on the current graph from nav toward x_u -> first result with a free slot
-// (else the smallest reached id with one) gets s->u -> the CTA marks what u
-// reaches.  The graph is edited by this kernel, so it is read with volatile
-// (coherent) loads; __syncthreads orders the CTA's global writes.
-// ---------------------------------------------------------------------------
-struct ConnectArgs {
-    const float4 *base4;
-    int dp4;
-    int64_t n;
-    int *adj, *deg;
-    int R, W, nav, L, H, hshift, max_steps;
-    uint32_t *reached;
-    int *queue, *out;
-};
-
-template <int G, int V, int U>
-__global__ void __launch_bounds__(256) connect_kernel(ConnectArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int sh_found, sh_size, sh_sel, sh_qtail, sh_capped;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    WarpSmem s = carve_warp_smem(smem, a.L, a.W, 0, a.H);
-    const int64_t nwords = (a.n + 31) >> 5;
-    const int tailbits = (int)(a.n & 31);
-    int64_t cursor = 0;
-    int added = 0, status = 0;
-    if (tid == 0) sh_capped = 0;
-    for (int64_t iter = 0; iter <= a.n; ++iter) {
-        if (tid == 0) sh_found = INT_MAX;
-        __syncthreads();
-        for (int64_t w0 = cursor; w0 < nwords; w0 += blockDim.x) {
-            int64_t w = w0 + tid;
-            if (w < nwords) {
-                uint32_t bits = ld_volatile(a.reached + w);
-                if (w == nwords - 1 && tailbits) bits |= ~((1u << tailbits) - 1u);
-                if (bits != 0xffffffffu) atomicMin(&sh_found, (int)(w * 32 + __ffs(~bits) - 1));
-            }
-            __syncthreads();
-            int f = sh_found;
-            __syncthreads();
-            if (f != INT_MAX) break;
-        }
-        const int u = sh_found;
-        if (u == INT_MAX) break;
-        cursor = u >> 5;
-        if (warp == 0) {
-            RowQuery<G, V> Q;
-            Q.load_row(a.base4 + (int64_t)u * a.dp4, a.dp4);
-            int csize = 0;
-            SearchOut o = warp_alg1<G, V, U, false, true>(Q, a.base4, a.dp4, GraphRef{a.adj, a.R}, a.nav,
-                                                           a.L, s, (uint32_t)a.H - 1, a.hshift,
-                                                           a.max_steps, -1, 0, csize);
-            if (lane_id() == 0) {
-                sh_size = o.size;
-                if (o.capped) sh_capped = 1;
-            }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int sel = -1;
-            for (int t = 0; t < sh_size; ++t) {
-                int id = kid(s.pool[t]);
-                if (ld_volatile(a.deg + id) < a.R) {
-                    sel = id;
-                    break;
-                }
-            }
-            sh_sel = sel;
-            sh_found = INT_MAX;
-        }
-        __syncthreads();
-        if (sh_sel < 0) {
-            for (int64_t x = tid; x < a.n; x += blockDim.x) {
-                uint32_t bits = ld_volatile(a.reached + (x >> 5));
-                if (((bits >> (x & 31)) & 1u) && ld_volatile(a.deg + x) < a.R) atomicMin(&sh_found, (int)x);
-            }
-            __syncthreads();
-            if (tid == 0) sh_sel = sh_found == INT_MAX ? -1 : sh_found;
-            __syncthreads();
-            if (sh_sel < 0) {
-                status = -5;
-                break;
-            }
-        }
-        if (tid == 0) {
-            const int sel = sh_sel;
-            const int dg = a.deg[sel];
-            a.adj[(int64_t)sel * a.R + dg] = u;
-            a.deg[sel] = dg + 1;
-            atomicOr(a.reached + (u >> 5), 1u << (u & 31));
-            a.queue[0] = u;
-            sh_qtail = 1;
-        }
-        ++added;
-        __syncthreads();
-        int head = 0;
-        for (;;) {
-            const int tail = sh_qtail;
-            if (head == tail) break;
-            __syncthreads();
-            const int64_t total = (int64_t)(tail - head) * a.R;
-            for (int64_t x = tid; x < total; x += blockDim.x) {
-                int node = ld_volatile(a.queue + head + x / a.R);
-                int v = ld_volatile(a.adj + (int64_t)node * a.R + x % a.R);
-                if (v < 0) continue;
-                uint32_t bit = 1u << (v & 31);
-                if (!(atomicOr(a.reached + (v >> 5), bit) & bit)) a.queue[atomicAdd(&sh_qtail, 1)] = v;
-            }
-            head = tail;
-            __syncthreads();
-        }
-    }
-    if (tid == 0) {
-        a.out[0] = added;
-        a.out[1] = status;
-        a.out[2] = sh_capped;
-    }
-}
-
-cudaError_t launch_connect(const ConnectLaunch &l, cudaStream_t st) {
-    ConnectArgs a;
-    a.base4 = reinterpret_cast<const float4 *>(l.base);
-    a.dp4 = l.dp / 4;
-    a.n = l.n;
-    a.adj = l.adj;
-    a.deg = l.deg;
-    a.R = l.R;
-    a.W = round32(l.R);
-    a.nav = l.nav;
-    a.L = l.L;
-    a.H = l.hash_slots;
-    a.hshift = 32 - log2i((unsigned)l.hash_slots);
-    a.max_steps = l.max_steps;
-    a.reached = l.reached;
-    a.queue = l.queue;
-    a.out = l.out;
-    size_t smem = warp_smem_bytes(a.L, a.W, 0, a.H);
-    cudaError_t err = cudaSuccess;
-    NSG_DISPATCH_DP4(a.dp4, {
-        auto kern = connect_kernel<G_, V_, U_>;
-        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err == cudaSuccess) {
-            kern<<<1, 256, smem, st>>>(a);
-            err = cudaGetLastError();
-        }
-    });
-    return err;
 }
 
 // ---------------------------------------------------------------------------

@@ -177,25 +177,6 @@ nsg_status navigate_run(const float *base, int64_t n, int d, const int *knn, int
 
 nsg_status connect_run(const float *bp, int64_t n, int dp, int *adj, int *deg, int R, int nav, int L,
                        int *n_added, cudaStream_t st) {
-    const int64_t nwords = (n + 31) / 32;
-    DevBuf<uint32_t> reached;
-    DevBuf<int> fa, fb, cnt, out;
-    NSG_CK(reached.alloc(nwords));
-    NSG_CK(fa.alloc(n));
-    NSG_CK(fb.alloc(n));
-    NSG_CK(cnt.alloc(2));
-    NSG_CK(out.alloc(4));
-    NSG_CK(cudaMemsetAsync(reached.p, 0, sizeof(uint32_t) * nwords, st));
-    NSG_CK(nsg::launch_bfs_seed(reached.p, nav, fa.p, cnt.p, st));
-    int nf = 1;
-    int *cur = fa.p, *nxt = fb.p;
-    for (int64_t level = 0; nf > 0 && level <= n; ++level) {
-        NSG_CK(cudaMemsetAsync(cnt.p + 1, 0, sizeof(int), st));
-        NSG_CK(nsg::launch_bfs_level(adj, R, cur, nf, nxt, cnt.p + 1, reached.p, st));
-        NSG_CK(cudaMemcpyAsync(&nf, cnt.p + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-        NSG_CK(cudaStreamSynchronize(st));
-        std::swap(cur, nxt);
-    }
     nsg::ConnectLaunch c;
     c.base = bp;
     c.n = n;
@@ -205,16 +186,10 @@ nsg_status connect_run(const float *bp, int64_t n, int dp, int *adj, int *deg, i
     c.R = R;
     c.nav = nav;
     c.L = L;
-    c.reached = reached.p;
-    c.queue = fa.p;
-    c.out = out.p;
     c.hash_slots = default_hash(L, R);
     c.max_steps = default_steps(L);
-    NSG_CK(cudaMemsetAsync(out.p, 0, 4 * sizeof(int), st));
-    NSG_CK(nsg::launch_connect(c, st));
     int h[4] = {0, 0, 0, 0};
-    NSG_CK(cudaMemcpyAsync(h, out.p, sizeof(h), cudaMemcpyDeviceToHost, st));
-    NSG_CK(cudaStreamSynchronize(st));
+    NSG_CK(nsg::run_connect(c, h, st));
     if (n_added) *n_added = h[0];
     if (h[1] == NSG_EDEGREE) return NSG_EDEGREE;
     return h[2] ? NSG_ESTEPCAP : NSG_OK;

@@ -76,15 +76,15 @@ struct ConnectLaunch {
     const float *base;  // [n][dp]
     int64_t n;
     int dp;
-    int *adj;  // [n][R]
+    int *adj;  // [n][R], edited in place
     int *deg;
     int R, nav, L;
-    uint32_t *reached;  // n bits, reach from nav already marked
-    int *queue;         // [n]
-    int *out;           // [0]=edges added, [1]=status, [2]=steps capped
     int hash_slots, max_steps;
 };
-cudaError_t launch_connect(const ConnectLaunch &a, cudaStream_t st);
+// Whole connectivity pass (reach from nav, then speculate/commit fix-up
+// batches).  out = {edges added, status, any search capped, re-searches}.
+// Allocates its scratch and synchronises the stream.
+cudaError_t run_connect(const ConnectLaunch &a, int out[4], cudaStream_t st);
 
 // Precision hits per query (Eq. 1).
 cudaError_t launch_recall(const int *ids, int ld_ids, const int *gt, int ld_gt, int64_t nq, int k,

@@ -427,6 +427,14 @@ cudaError_t launch_knn_tc(const KnnLaunch &l, int *used, cudaStream_t st) {
     CUtensorMap mA, mB;
     const int64_t arows = l.self_join ? l.n - l.q0 : l.nq;
     if (!make_map(&mA, qsrc, arows, dk, TC_M) || !make_map(&mB, xb.p, l.n, dk, TC_N)) return cudaSuccess;
+    // the rows' sorted lists live in the output arrays: distances are needed
+    // even when the caller asked for ids only
+    Scratch<float> d2s;
+    float *d2out = l.d2;
+    if (!d2out) {
+        if ((e = d2s.alloc((size_t)l.nq * l.k)) != cudaSuccess) return e;
+        d2out = d2s.p;
+    }
     TcArgs a;
     a.qn = qnorm;
     a.xn = xn.p;
@@ -437,7 +445,7 @@ cudaError_t launch_knn_tc(const KnnLaunch &l, int *used, cudaStream_t st) {
     a.KL = l.k;
     a.ntiles = (int)ntiles;
     a.ids = l.ids;
-    a.d2 = l.d2;
+    a.d2 = d2out;
     a.err = flag.p + 1;
     const int64_t grid = (l.nq + TC_M - 1) / TC_M;
     if (dk == 64) {

@@ -14,7 +14,8 @@
 //   * search-and-collect on the kNN graph (Alg. 2 lines 5-6): every computed
 //     key except the node itself is also merged into a collect list of the C
 //     smallest keys,
-//   * the connectivity pass (Alg. 2 line 26), on a graph the same kernel is
+//   * the connectivity pass (Alg. 2 line 26): speculative searches that also
+//     log the ids they expand, and re-searches on a graph the same kernel is
 //     editing (plain coherent loads instead of the read-only path).
 #pragma once
 
@@ -82,7 +83,8 @@ __device__ __forceinline__ void collect_merge(WarpSmem &s, int m, int excl, int 
 template <int G, int V, int U, bool COLLECT, bool COHERENT>
 __device__ SearchOut warp_alg1(const RowQuery<G, V> &Q, const float4 *__restrict__ base4, int dp4,
                                GraphRef g, int start, int L, WarpSmem &s, uint32_t hmask, int hshift,
-                               int max_steps, int excl, int C, int &csize) {
+                               int max_steps, int excl, int C, int &csize, int *xlog = nullptr,
+                               int xcap = 0) {
     const unsigned lane = lane_id();
     SearchOut o;
     o.size = 0;
@@ -123,6 +125,7 @@ __device__ SearchOut warp_alg1(const RowQuery<G, V> &Q, const float4 *__restrict
         __syncwarp();
         if (lane == 0) s.pool[i] = e | CHK;
         const int u = kid(e);
+        if (xlog != nullptr && lane == 0 && o.n_expand <= xcap) xlog[o.n_expand - 1] = u;  // expanded ids
         const int *row = g.adj + (int64_t)u * g.width;
         int m = 0;
         for (int b = 0; b < g.width; b += 32) {

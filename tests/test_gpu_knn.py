@@ -80,3 +80,12 @@ def test_knn_large_d_uses_scan_bit_exact(nsg):
     ids, d2 = nsg.nsg_knn_init(T(base), 30)
     rid, rd2 = oracle.knn_rows(base, 30)
     assert np.array_equal(H(ids), rid) and np.array_equal(H(d2), rd2)
+
+
+def test_knn_init_ids_only(nsg):
+    # the build asks for ids only; the tensor-core path keeps its lists in scratch then
+    base = datagen.uniform_int(1500, 64, seed=66)
+    ids, d2 = nsg.nsg_knn_init(T(base), 20, with_d2=False)
+    assert d2 is None
+    rid, _ = oracle.knn_rows(base, 20)
+    assert np.array_equal(H(ids), rid)
