@@ -114,6 +114,24 @@ nsg_status nsg_navigate(const float *base_dev, int64_t n, int32_t d, const int32
                         int32_t *nav_host, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * nsg_navigate_noalloc: nsg_navigate without any device allocation.  The
+ *   paper has no counterpart; it exists for callers that may not allocate
+ *   device memory themselves (a framework's caching allocator owns HBM, or a
+ *   serving loop cannot afford cudaFree's device-wide synchronisation).
+ *   Same arguments, result and synchronisation as nsg_navigate.  Its visited
+ *   bitmap is a fixed array inside the library (held by every GPU that loads
+ *   it until the process exits), so n <= NSG_NOALLOC_MAX_N, else NSG_EINVAL.
+ *   The first call on a device looks the array up (cudaGetSymbolAddress); make
+ *   that first call before any stream capture.  All calls on a device share
+ *   the array (each clears what it uses first): calls that overlap on the GPU
+ *   race and must be serialised by the caller.
+ * ------------------------------------------------------------------------- */
+#define NSG_NOALLOC_MAX_N 16777216
+nsg_status nsg_navigate_noalloc(const float *base_dev, int64_t n, int32_t d, const int32_t *knn_ids_dev,
+                                int32_t K, const double *centroid_dev, int32_t start, int32_t L,
+                                int32_t *nav_host, void *stream);
+
+/* ---------------------------------------------------------------------------
  * A5. Search-and-collect (Alg. 2 lines 5-8; Section 3.4 step iii; Fig. 4) for
  *   nodes v0 .. v0+nv-1: Alg. 1 on the kNN graph from `nav` with query x_v
  *   and pool L; every node whose distance was computed, plus v's K kNN

@@ -58,6 +58,7 @@ SIGNATURES = [
     ("nsg_knn_query", [P, i64, i32, P, i64, i32, P, P, P], i32),
     ("nsg_centroid", [P, i64, i32, P, P], i32),
     ("nsg_navigate", [P, i64, i32, P, i32, P, i32, i32, P, P], i32),
+    ("nsg_navigate_noalloc", [P, i64, i32, P, i32, P, i32, i32, P, P], i32),
     ("nsg_collect", [P, i64, i32, P, i32, i32, i32, i32, i64, i64, P, P, P, P, P], i32),
     ("nsg_prune", [P, i64, i32, P, P, P, i32, i32, i64, i64, P, P, P], i32),
     ("nsg_connect", [P, i64, i32, P, P, i32, i32, i32, P, P], i32),
@@ -143,6 +144,19 @@ def nsg_navigate(base, knn, centroid, start, L):
     nav = C.c_int32(0)
     _check(lib().nsg_navigate(_ptr(base), n, d, _ptr(knn), knn.shape[1], _ptr(centroid), int(start), L,
                               C.byref(nav), _stream()), "nsg_navigate")
+    return nav.value
+
+
+def nsg_navigate_noalloc(base, knn, centroid, start, L):
+    """nsg_navigate for callers that may not allocate device memory: the
+    visited bitmap is a fixed array inside the library (n <= 16,777,216);
+    calls sharing a device must not overlap on the GPU."""
+    base, knn = _dev(base, torch.float32), _dev(knn, torch.int32)
+    centroid = _dev(centroid, torch.float64)
+    n, d = base.shape
+    nav = C.c_int32(0)
+    _check(lib().nsg_navigate_noalloc(_ptr(base), n, d, _ptr(knn), knn.shape[1], _ptr(centroid), int(start),
+                                      L, C.byref(nav), _stream()), "nsg_navigate_noalloc")
     return nav.value
 
 

@@ -300,6 +300,8 @@ double since_ms(std::chrono::steady_clock::time_point t0) {
 
 namespace nsg {
 
+void record_cuda_error(cudaError_t e, const char *what) { cuda_fail(e, what); }
+
 int sm_count() {
     static int cache[64] = {0};
     int dev = 0;

@@ -114,6 +114,9 @@ cudaError_t launch_knn_tc(const KnnLaunch &a, int *used, cudaStream_t st);
 // Padding copy [n][d] -> [n][dp] (zeros in the pad).
 cudaError_t launch_pad_rows(const float *src, int64_t n, int d, float *dst, int dp, cudaStream_t st);
 
+// Remember a CUDA error for nsg_last_cuda_error() (calling thread).
+void record_cuda_error(cudaError_t e, const char *what);
+
 // Device properties cached per device.
 int sm_count();
 size_t smem_optin();
