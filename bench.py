@@ -7,6 +7,11 @@ paper's Alg. 2 at K=100, L=40, R=50, C=500.  The pool size L is swept over
 100, 125, ..., 400 (k=100); the reported point is the highest-QPS L whose
 mean recall@10 (Eq. 1, against the exact ground truth) is >= 0.95.
 
+Forms: plain (FP32 traversal, exactly Alg. 1) and the precision forms (BF16
+or FP8-e4m3 traversal distances with FP32 accumulation, FP32 re-rank of the
+final pool when the copy is lossy).  `value` is the form with the highest QPS
+at recall@10 >= 0.95 ("chosen"); `plain` holds the plain form beside it.
+
 A step = one nsg_search_ex launch over the whole 10,000-query batch, inputs
 resident in HBM.  The base (512 MB) is larger than L2 (129 MB).
 `e2e` repeats the step through the public API with pinned host buffers:
@@ -209,59 +214,79 @@ def main():
     t0 = time.perf_counter()
     idx = capi.nsg_build(bt, BUILD["K"], BUILD["L"], BUILD["R"], BUILD["C"], seed=0)
     build_s = time.perf_counter() - t0
-    info = idx.info()
     gt, _ = capi.nsg_knn_query(bt, qt, 10)
 
-    # sweep L: recall@10 and a quick timing per point
+    # the forms: plain FP32 traversal, and the precision forms (BF16 / FP8-e4m3
+    # traversal with FP32 accumulation; FP32 re-rank of the pool when the copy is lossy)
+    forms = {"plain": capi.SearchParams(0, 0, capi.PREC_F32, 0)}
+    for name, prec in (("bf16", capi.PREC_BF16), ("fp8", capi.PREC_FP8)):
+        idx.prepare(prec)
+        forms[name] = capi.SearchParams(0, 0, prec, 0, -1)
+    info = idx.info()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = None
-    sweep = []
-    for L in L_GRID:
-        out = idx.search_ex(qt, K_RESULTS, L, out=out, counters=False)
-        hits = capi.nsg_recall(out["ids"][:, :10].contiguous(), gt, 10)
-        rec = hits.sum().item() / (10.0 * nq)
+
+    def timed(params, L, reps):
+        nonlocal out
         ev0.record(st)
-        for _ in range(2):
-            idx.search_ex(qt, K_RESULTS, L, out=out, counters=False)
+        for _ in range(reps):
+            out = idx.search_ex(qt, K_RESULTS, L, params=params, out=out, counters=False)
         ev1.record(st)
         ev1.synchronize()
-        ms = ev0.elapsed_time(ev1) / 2
-        sweep.append({"L": L, "recall10": rec, "qps": nq / (ms / 1e3)})
-    ok = [s for s in sweep if s["recall10"] >= TARGET]
-    chosen = max(ok, key=lambda s: s["qps"]) if ok else max(sweep, key=lambda s: s["recall10"])
-    L = chosen["L"]
+        return ev0.elapsed_time(ev1) / reps
 
-    # algorithmic bytes at the chosen L: unique distance and expansion counts
-    big = capi.SearchParams(0, 16384, capi.PREC_F32, 0)
+    def recall10(o):
+        return capi.nsg_recall(o["ids"][:, :10].contiguous(), gt, 10).sum().item() / (10.0 * nq)
+
+    # sweep L per form: recall@10 and a quick timing per point
+    sweeps, best = {}, {}
+    for name, prm in forms.items():
+        pts = []
+        for L in L_GRID:
+            out = idx.search_ex(qt, K_RESULTS, L, params=prm, out=out, counters=False)
+            rec = recall10(out)
+            ms = timed(prm, L, 2)
+            pts.append({"L": L, "recall10": rec, "qps": nq / (ms / 1e3)})
+        sweeps[name] = pts
+        ok = [p for p in pts if p["recall10"] >= TARGET]
+        best[name] = max(ok, key=lambda p: p["qps"]) if ok else None
+    cands = {k: v for k, v in best.items() if v is not None}
+    chosen_form = max(cands, key=lambda k: cands[k]["qps"]) if cands else "plain"
+    plain_L = best["plain"]["L"] if best["plain"] else L_GRID[-1]
+    L = cands[chosen_form]["L"] if cands else L_GRID[-1]
+    prm = forms[chosen_form]
+
+    # algorithmic bytes at the chosen point: unique distance and expansion counts
+    big = capi.SearchParams(0, 16384, prm.precision, 0, prm.rerank)
     cnt = idx.search_ex(qt, K_RESULTS, L, params=big)
     n_dist = cnt["n_dist"].to(torch.int64).sum().item()
     n_expand = cnt["n_expand"].to(torch.int64).sum().item()
     R = info["R"]
-    bytes_launch = n_dist * d * 4 + n_expand * (R * 4) + nq * (d * 4 + K_RESULTS * 8)
+    row_bytes = {"plain": d * 4, "bf16": ((d + 7) // 8) * 16, "fp8": ((d + 15) // 16) * 16}[chosen_form]
+    lossy = {"plain": False, "bf16": info["has_bf16"] == 1, "fp8": info["has_fp8"] == 1}[chosen_form]
+    bytes_launch = (n_dist * row_bytes + n_expand * R * 4 + nq * (d * 4 + K_RESULTS * 8)
+                    + (nq * L * d * 4 if lossy else 0))
 
     # timed region: inputs resident in HBM, one search launch per step
     for _ in range(args.warmup):
-        idx.search_ex(qt, K_RESULTS, L, out=out, counters=False)
+        idx.search_ex(qt, K_RESULTS, L, params=prm, out=out, counters=False)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = ClockSampler(local)
     time.sleep(0.4)
     torch.cuda.synchronize()
-    ev0.record(st)
-    for _ in range(args.steps):
-        idx.search_ex(qt, K_RESULTS, L, out=out, counters=False)
-    ev1.record(st)
+    ms_step = timed(prm, L, args.steps)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    ms_step = ev0.elapsed_time(ev1) / args.steps
+    rec_chosen = recall10(out)
+    ms_plain = timed(forms["plain"], plain_L, args.steps)
+    rec_plain = recall10(out)
     if world > 1:
-        t = torch.tensor([ms_step], device="cuda")
+        t = torch.tensor([ms_step, ms_plain], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = t.item()
+        ms_step, ms_plain = t[0].item(), t[1].item()
         dist.barrier()
-    final_hits = capi.nsg_recall(out["ids"][:, :10].contiguous(), gt, 10)
-    recall10 = final_hits.sum().item() / (10.0 * nq)
 
     # end to end through the public API with pinned host buffers
     qh = torch.from_numpy(q).pin_memory()
@@ -272,7 +297,7 @@ def main():
             torch.cuda.synchronize()
             e2e_t0 = time.perf_counter()
         qd.copy_(qh, non_blocking=True)
-        o = idx.search_ex(qd, K_RESULTS, L, out=out, counters=False)
+        o = idx.search_ex(qd, K_RESULTS, L, params=prm, out=out, counters=False)
         ids_h.copy_(o["ids"], non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_ms = 1e3 * (time.perf_counter() - e2e_t0) / args.steps
@@ -284,11 +309,11 @@ def main():
     peak, peak_kind = peaks()
     achieved = bytes_launch / (ms_step / 1e3) / 1e9
     src = kernel_source_hash()
-    tr = NCU_TRAFFIC.get(src)
+    tr = NCU_TRAFFIC.get((src, chosen_form, L))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": (tr * nq if tr else None),
-                "peak_kind": peak_kind, "kernel": "search_kernel", "algorithmic_bytes": bytes_launch,
-                "kernel_src": src}
+                "peak_kind": peak_kind, "kernel": f"search_kernel ({chosen_form})",
+                "algorithmic_bytes": bytes_launch, "kernel_src": src}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -298,12 +323,16 @@ def main():
         line = {
             "metric": METRIC, "value": world * nq / (ms_step / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"plain": "f32", "bf16": "bf16->f32", "fp8": "fp8e4m3->f32"}[chosen_form],
             "data": "synthetic",
             "config": {"workload": "sift-shaped 1,000,000 x 128 int 0..255 GMM(100), 10,000 queries",
-                       "form": "plain", "build": BUILD, "k": K_RESULTS, "L": L,
-                       "recall10": recall10, "target_recall10": TARGET, "parallelism": f"replicas{world}",
+                       "form": chosen_form, "build": BUILD, "k": K_RESULTS, "L": L,
+                       "recall10": rec_chosen, "target_recall10": TARGET, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (512 MB base)"},
+            "plain": {"value": world * nq / (ms_plain / 1e3), "ms_per_step": ms_plain, "L": plain_L,
+                      "recall10": rec_plain},
+            "chosen_over_plain": ms_plain / ms_step,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": world * nq / (e2e_ms / 1e3), "unit": UNIT,
@@ -314,9 +343,10 @@ def main():
             "build_ms": {k: info[k] for k in ("ms_knn", "ms_centroid_nav", "ms_collect", "ms_prune",
                                                "ms_connect", "ms_total")},
             "index": {"avg_degree": info["avg_degree"], "max_degree": info["max_degree"],
-                      "fixup_edges": info["n_fixup_edges"], "nav": info["nav"]},
+                      "fixup_edges": info["n_fixup_edges"], "fixup_researched": info["n_fixup_searches"],
+                      "nav": info["nav"], "bf16_exact": info["has_bf16"] == 2, "fp8_scale": info["fp8_scale"]},
             "per_query": {"n_expand": n_expand / nq, "n_dist": n_dist / nq},
-            "sweep": sweep,
+            "sweep": sweeps,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -53,9 +53,11 @@ typedef enum { NSG_PREC_F32 = 0, NSG_PREC_BF16 = 1, NSG_PREC_FP8 = 2 } nsg_preci
 
 typedef struct {
     int32_t max_steps;     /* expansion cap per query; <= 0 -> 16*L + 4096 */
-    int32_t hash_slots;    /* visited-hash slots per query (power of 2); <= 0 -> auto */
-    int32_t precision;     /* nsg_precision */
+    int32_t hash_slots;    /* visited-hash slots per query (power of 2, 64..65536); <= 0 -> auto */
+    int32_t precision;     /* nsg_precision of the traversal distances */
     int32_t warps_per_cta; /* <= 0 -> auto */
+    int32_t rerank;        /* BF16/FP8: re-rank the final pool with FP32 rows (1), not (0),
+                              or only when the copy is lossy (-1) */
 } nsg_search_params;
 
 typedef struct {
@@ -67,11 +69,12 @@ typedef struct {
     double avg_degree;     /* mean out-degree (AOD of Table 2) */
     int64_t n_fixup_edges; /* edges added by the connectivity pass */
     int64_t device_bytes;  /* device memory held by the index */
-    int32_t has_bf16;      /* a BF16 copy of the base is held */
-    int32_t has_fp8;       /* an FP8-e4m3 copy of the base is held */
+    int32_t has_bf16;      /* BF16 copy: 0 none, 1 lossy, 2 every value exact */
+    int32_t has_fp8;       /* FP8-e4m3 copy: 0 none, 1 lossy, 2 every value exact */
     float fp8_scale;       /* x_fp8 = x * fp8_scale (0 when absent) */
     /* build phase wall times in milliseconds (0 when not built here) */
     float ms_knn, ms_centroid_nav, ms_collect, ms_prune, ms_connect, ms_total;
+    int64_t n_fixup_searches; /* fix-ups whose speculative search was stale and ran again */
 } nsg_index_info_t;
 
 /* Human-readable name of a status code (static string). */
@@ -197,6 +200,11 @@ nsg_status nsg_index_from_graph(const float *base_dev, int64_t n, int32_t d, con
  * nsg_search_ex: same with parameters and optional per-query outputs
  *   n_expand_dev [nq] (nodes checked), n_dist_dev [nq] (distances computed),
  *   status_dev [nq] (0 or NSG_ESTEPCAP).  Does not synchronise.
+ *   params->precision BF16 / FP8 (after nsg_index_prepare): traversal
+ *   distances on that copy with FP32 accumulation; with re-rank, the L pool
+ *   entries are measured again on the FP32 rows and the k smallest returned
+ *   (d2 then holds FP32 squared distances; without re-rank, FP8 distances are
+ *   in scaled units).
  * ------------------------------------------------------------------------- */
 nsg_status nsg_search(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k,
                       int32_t L, int32_t *ids_dev, float *d2_dev, void *stream);
@@ -222,6 +230,11 @@ nsg_status nsg_recall(const int32_t *ids_dev, int32_t ld_ids, const int32_t *gt_
  * nsg_free: releases the index (NULL is ignored).
  * ------------------------------------------------------------------------- */
 nsg_status nsg_index_info(const nsg_index *idx, nsg_index_info_t *info);
+/* Low-precision copy of the base for the precision forms of nsg_search_ex
+ *   (NSG_PREC_BF16: round to nearest; NSG_PREC_FP8: e4m3 of x * s with
+ *   s = 448 / max|x|, saturating).  Owned by the index; a no-op when present.
+ *   Synchronises the stream. */
+nsg_status nsg_index_prepare(nsg_index *idx, int32_t precision, void *stream);
 nsg_status nsg_index_graph(const nsg_index *idx, int32_t *adj_dev, int32_t *deg_dev, void *stream);
 nsg_status nsg_save(const nsg_index *idx, const char *path);
 nsg_status nsg_load(const char *path, void *stream, nsg_index **out);

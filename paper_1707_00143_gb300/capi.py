@@ -32,7 +32,10 @@ class NsgError(RuntimeError):
 
 class SearchParams(C.Structure):
     _fields_ = [("max_steps", C.c_int32), ("hash_slots", C.c_int32), ("precision", C.c_int32),
-                ("warps_per_cta", C.c_int32)]
+                ("warps_per_cta", C.c_int32), ("rerank", C.c_int32)]
+
+    def __init__(self, max_steps=0, hash_slots=0, precision=0, warps_per_cta=0, rerank=-1):
+        super().__init__(max_steps, hash_slots, precision, warps_per_cta, rerank)
 
 
 class IndexInfo(C.Structure):
@@ -41,7 +44,7 @@ class IndexInfo(C.Structure):
                 ("device_bytes", C.c_int64), ("has_bf16", C.c_int32), ("has_fp8", C.c_int32),
                 ("fp8_scale", C.c_float), ("ms_knn", C.c_float), ("ms_centroid_nav", C.c_float),
                 ("ms_collect", C.c_float), ("ms_prune", C.c_float), ("ms_connect", C.c_float),
-                ("ms_total", C.c_float)]
+                ("ms_total", C.c_float), ("n_fixup_searches", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -68,6 +71,7 @@ SIGNATURES = [
     ("nsg_search_ex", [P, P, i64, i32, i32, P, P, P, P, P, P, P], i32),
     ("nsg_recall", [P, i32, P, i32, i64, i32, P, P], i32),
     ("nsg_index_info", [P, P], i32),
+    ("nsg_index_prepare", [P, i32, P], i32),
     ("nsg_index_graph", [P, P, P, P], i32),
     ("nsg_save", [P, C.c_char_p], i32),
     ("nsg_load", [C.c_char_p, P, P], i32),
@@ -226,6 +230,10 @@ class Index:
         inf = IndexInfo()
         _check(lib().nsg_index_info(self.h, C.byref(inf)), "nsg_index_info")
         return inf.as_dict()
+
+    def prepare(self, precision):
+        """Build the BF16 (1) or FP8-e4m3 (2) copy used by the precision forms."""
+        _check(lib().nsg_index_prepare(self.h, precision, _stream()), "nsg_index_prepare")
 
     def graph(self):
         inf = self.info()

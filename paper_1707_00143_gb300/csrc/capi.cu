@@ -20,9 +20,15 @@ struct nsg_index {
     int *adj = nullptr;     // [n][R], -1 padded
     int *deg = nullptr;     // [n]
     int *flag = nullptr;    // [4] device scratch for nsg_search's cap check
+    // low-precision copies, indexed by nsg_precision (1 = BF16, 2 = FP8-e4m3)
+    void *lowp[3] = {nullptr, nullptr, nullptr};
+    int lowp_dpl[3] = {0, 0, 0};        // values per row (16-byte multiple)
+    float lowp_scale[3] = {1, 1, 1};    // query multiplier
+    int lowp_exact[3] = {0, 0, 0};      // every value survived the conversion
     int max_degree = 0;
     double avg_degree = 0.0;
     int64_t n_fixup = 0;
+    int64_t n_fixup_searches = 0;  // fix-ups whose speculative search was stale and ran again
     float ms[6] = {0, 0, 0, 0, 0, 0};
 };
 
@@ -176,7 +182,7 @@ nsg_status navigate_run(const float *base, int64_t n, int d, const int *knn, int
 }
 
 nsg_status connect_run(const float *bp, int64_t n, int dp, int *adj, int *deg, int R, int nav, int L,
-                       int *n_added, cudaStream_t st) {
+                       int *n_added, cudaStream_t st, int *n_research = nullptr) {
     nsg::ConnectLaunch c;
     c.base = bp;
     c.n = n;
@@ -191,6 +197,7 @@ nsg_status connect_run(const float *bp, int64_t n, int dp, int *adj, int *deg, i
     int h[4] = {0, 0, 0, 0};
     NSG_CK(nsg::run_connect(c, h, st));
     if (n_added) *n_added = h[0];
+    if (n_research) *n_research = h[3];
     if (h[1] == NSG_EDEGREE) return NSG_EDEGREE;
     return h[2] ? NSG_ESTEPCAP : NSG_OK;
 }
@@ -289,6 +296,8 @@ void destroy(nsg_index *ix) {
     if (ix->adj) cudaFree(ix->adj);
     if (ix->deg) cudaFree(ix->deg);
     if (ix->flag) cudaFree(ix->flag);
+    for (void *p : ix->lowp)
+        if (p) cudaFree(p);
     delete ix;
 }
 
@@ -511,10 +520,11 @@ nsg_status nsg_build(const float *base_dev, int64_t n, int32_t d, int32_t K, int
     knn.alloc(0);  // release the kNN graph before the connectivity pass
     // A7: connectivity
     t0 = std::chrono::steady_clock::now();
-    int added = 0;
-    if (!s) s = connect_run(base.p, n, ix->dp, adj.p, deg.p, R, ix->nav, L, &added, st);
+    int added = 0, research = 0;
+    if (!s) s = connect_run(base.p, n, ix->dp, adj.p, deg.p, R, ix->nav, L, &added, st, &research);
     ix->ms[4] = (float)since_ms(t0);
     ix->n_fixup = added;
+    ix->n_fixup_searches = research;
     if (s) {
         destroy(ix);
         return s;
@@ -601,9 +611,10 @@ nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t
     if (!idx || k < 1 || L < k || L > 1024 || nq < 0 || nq >= INT32_MAX) return NSG_EINVAL;
     if (nq == 0) return NSG_OK;
     if (!queries_dev || !ids_dev) return NSG_EINVAL;
-    nsg_search_params p = {0, 0, NSG_PREC_F32, 0};
+    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1};
     if (params) p = *params;
-    if (p.precision != NSG_PREC_F32) return NSG_EINVAL;
+    if (p.precision < NSG_PREC_F32 || p.precision > NSG_PREC_FP8) return NSG_EINVAL;
+    if (p.precision != NSG_PREC_F32 && !idx->lowp[p.precision]) return NSG_EINVAL;  // nsg_index_prepare first
     if (p.hash_slots > 0 && (p.hash_slots < 64 || (p.hash_slots & (p.hash_slots - 1)) || p.hash_slots > 65536))
         return NSG_EINVAL;
     nsg::SearchLaunch l;
@@ -627,7 +638,48 @@ nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t
     l.n_dist = n_dist_dev;
     l.status = status_dev;
     l.any_capped = nullptr;
+    if (p.precision != NSG_PREC_F32) {
+        l.precision = p.precision;
+        l.lowp = idx->lowp[p.precision];
+        l.lowp_chunks = idx->lowp_dpl[p.precision] * (p.precision == NSG_PREC_BF16 ? 2 : 1) / 16;
+        l.lowp_scale = idx->lowp_scale[p.precision];
+        // auto: re-rank unless the copy holds every value exactly (then its keys are the FP32 keys)
+        l.rerank = p.rerank < 0 ? !idx->lowp_exact[p.precision] : p.rerank != 0;
+    }
     NSG_CK(nsg::launch_search(l, S(stream)));
+    return NSG_OK;
+}
+
+nsg_status nsg_index_prepare(nsg_index *idx, int32_t precision, void *stream) {
+    if (!idx || (precision != NSG_PREC_BF16 && precision != NSG_PREC_FP8)) return NSG_EINVAL;
+    if (idx->lowp[precision]) return NSG_OK;
+    cudaStream_t st = S(stream);
+    const int epc = precision == NSG_PREC_BF16 ? 8 : 16;  // values per 16-byte chunk
+    const int dpl = (idx->d + epc - 1) / epc * epc;
+    float scale = 1.0f;
+    DevBuf<int> flags;
+    NSG_CK(flags.alloc(2));
+    NSG_CK(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), st));
+    if (precision == NSG_PREC_FP8) {  // per-tensor scale: the largest |x| maps to 448 (e4m3 max)
+        unsigned bits = 0;
+        NSG_CK(nsg::launch_absmax(idx->base, idx->n * idx->dp, reinterpret_cast<unsigned *>(flags.p), st));
+        NSG_CK(cudaMemcpyAsync(&bits, flags.p, sizeof(bits), cudaMemcpyDeviceToHost, st));
+        NSG_CK(cudaStreamSynchronize(st));
+        float mx;
+        std::memcpy(&mx, &bits, sizeof(mx));
+        scale = mx > 0.0f ? 448.0f / mx : 1.0f;
+        NSG_CK(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), st));
+    }
+    DevBuf<unsigned char> buf;
+    NSG_CK(buf.alloc((size_t)idx->n * dpl * (precision == NSG_PREC_BF16 ? 2 : 1)));
+    NSG_CK(nsg::launch_to_lowp(idx->base, idx->n, idx->dp, idx->d, precision, scale, buf.p, dpl, flags.p, st));
+    int inexact = 0;
+    NSG_CK(cudaMemcpyAsync(&inexact, flags.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NSG_CK(cudaStreamSynchronize(st));
+    idx->lowp[precision] = buf.release();
+    idx->lowp_dpl[precision] = dpl;
+    idx->lowp_scale[precision] = scale;
+    idx->lowp_exact[precision] = !inexact;
     return NSG_OK;
 }
 
@@ -686,6 +738,12 @@ nsg_status nsg_index_info(const nsg_index *idx, nsg_index_info_t *info) {
     info->avg_degree = idx->avg_degree;
     info->n_fixup_edges = idx->n_fixup;
     info->device_bytes = (int64_t)idx->n * idx->dp * 4 + (int64_t)idx->n * idx->R * 4 + idx->n * 4 + 16;
+    info->has_bf16 = idx->lowp[NSG_PREC_BF16] ? (idx->lowp_exact[NSG_PREC_BF16] ? 2 : 1) : 0;
+    info->has_fp8 = idx->lowp[NSG_PREC_FP8] ? (idx->lowp_exact[NSG_PREC_FP8] ? 2 : 1) : 0;
+    info->fp8_scale = idx->lowp[NSG_PREC_FP8] ? idx->lowp_scale[NSG_PREC_FP8] : 0.0f;
+    info->n_fixup_searches = idx->n_fixup_searches;
+    for (int p = 1; p <= 2; ++p)
+        if (idx->lowp[p]) info->device_bytes += (int64_t)idx->n * idx->lowp_dpl[p] * (p == 1 ? 2 : 1);
     info->ms_knn = idx->ms[0];
     info->ms_centroid_nav = idx->ms[1];
     info->ms_collect = idx->ms[2];

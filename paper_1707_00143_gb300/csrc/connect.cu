@@ -119,11 +119,11 @@ __global__ void __launch_bounds__(256) speculate_kernel(SpecArgs a) {
     int csize = 0;
     for (int j = blockIdx.x * wpb + warp; j < cnt; j += gridDim.x * wpb) {
         const int u = a.list[j];
-        RowQuery<G, V> Q;
-        Q.load_row(a.base4 + (int64_t)u * a.dp4, a.dp4);
-        SearchOut o = warp_alg1<G, V, U, false, false>(Q, a.base4, a.dp4, GraphRef{a.adj, a.R}, a.nav, a.L, s,
-                                                        (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0, csize,
-                                                        a.xlog + (int64_t)j * a.xcap, a.xcap);
+        DistF32<G, V, U> dist{{}, a.base4, a.dp4};
+        dist.Q.load_row(a.base4 + (int64_t)u * a.dp4, a.dp4);
+        SearchOut o = warp_alg1<false, false>(dist, GraphRef{a.adj, a.R}, a.nav, a.L, s, (uint32_t)a.H - 1,
+                                              a.hshift, a.max_steps, -1, 0, csize, a.xlog + (int64_t)j * a.xcap,
+                                              a.xcap);
         for (int t = lane; t < a.L; t += 32) a.pools[(int64_t)j * a.L + t] = t < o.size ? s.pool[t] : KEY_INF;
         if (lane == 0) {
             a.psize[j] = o.size;
@@ -173,12 +173,11 @@ __global__ void __launch_bounds__(256) commit_kernel(CommitArgs a) {
         int size;
         if (sh_flag) {  // the snapshot is stale for this u: search the current graph
             if (warp == 0) {
-                RowQuery<G, V> Q;
-                Q.load_row(a.base4 + (int64_t)u * a.dp4, a.dp4);
+                DistF32<G, V, U> dist{{}, a.base4, a.dp4};
+                dist.Q.load_row(a.base4 + (int64_t)u * a.dp4, a.dp4);
                 int csize = 0;
-                SearchOut o = warp_alg1<G, V, U, false, true>(Q, a.base4, a.dp4, GraphRef{a.adj, a.R}, a.nav, a.L,
-                                                               s, (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
-                                                               csize);
+                SearchOut o = warp_alg1<false, true>(dist, GraphRef{a.adj, a.R}, a.nav, a.L, s, (uint32_t)a.H - 1,
+                                                     a.hshift, a.max_steps, -1, 0, csize);
                 if (lane_id() == 0) {
                     sh_size = o.size;
                     if (o.capped) sh_flag = 2;

@@ -25,8 +25,21 @@ struct SearchLaunch {
     float *d2;
     int *n_expand, *n_dist, *status;
     int *any_capped;  // device flag, nullable
+    // precision forms: traversal on a BF16 / FP8 copy, FP32 re-rank of the pool
+    int precision = 0;  // 0 FP32, 1 BF16, 2 FP8-e4m3
+    const void *lowp = nullptr;
+    int lowp_chunks = 0;  // 16-byte chunks per low-precision row
+    float lowp_scale = 1.0f;
+    int rerank = 0;
 };
 cudaError_t launch_search(const SearchLaunch &a, cudaStream_t st);
+
+// Largest |x| over `count` floats (bits of a non-negative float, atomicMax).
+cudaError_t launch_absmax(const float *x, int64_t count, unsigned *out_bits, cudaStream_t st);
+// [n][dp] FP32 -> [n][dpl] BF16 (precision 1) or FP8-e4m3 of x*scale (precision 2),
+// zero padded; *inexact is raised when some value does not survive the round trip.
+cudaError_t launch_to_lowp(const float *src, int64_t n, int dp, int d, int precision, float scale, void *dst,
+                           int dpl, int *inexact, cudaStream_t st);
 
 // Search-and-collect on the kNN graph for nodes v0..v0+nv-1.
 struct CollectLaunch {

@@ -1,0 +1,62 @@
+// lowp.cu -- building the BF16 / FP8-e4m3 copies of the base used by the
+// precision forms of the search.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace nsg {
+
+__global__ void absmax_kernel(const float *__restrict__ x, int64_t count, unsigned *out) {
+    float m = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(NSG_FULL, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+cudaError_t launch_absmax(const float *x, int64_t count, unsigned *out_bits, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    int64_t blocks = (count + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    absmax_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, st>>>(x, count, out_bits);
+    return cudaGetLastError();
+}
+
+template <int P>
+__global__ void to_lowp_kernel(const float *__restrict__ src, int64_t n, int dp, int d, float scale, void *dst,
+                               int dpl, int *inexact) {
+    const int64_t total = n * dpl;
+    bool bad = false;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = x / dpl;
+        const int c = (int)(x % dpl);
+        const float v = c < d ? src[r * dp + c] : 0.0f;
+        if (P == 1) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            reinterpret_cast<__nv_bfloat16 *>(dst)[x] = h;
+            bad |= __bfloat162float(h) != v;
+        } else {
+            const __nv_fp8_storage_t h = __nv_cvt_float_to_fp8(v * scale, __NV_SATFINITE, __NV_E4M3);
+            reinterpret_cast<__nv_fp8_storage_t *>(dst)[x] = h;
+            const __half_raw hr = __nv_cvt_fp8_to_halfraw(h, __NV_E4M3);
+            bad |= __half2float(*reinterpret_cast<const __half *>(&hr)) != v * scale;
+        }
+    }
+    if (__any_sync(NSG_FULL, bad) && (threadIdx.x & 31) == 0) atomicOr(inexact, 1);
+}
+
+cudaError_t launch_to_lowp(const float *src, int64_t n, int dp, int d, int precision, float scale, void *dst,
+                           int dpl, int *inexact, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n * dpl + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 16;
+    const int g = (int)(blocks < cap ? blocks : cap);
+    if (precision == 1) to_lowp_kernel<1><<<g, 256, 0, st>>>(src, n, dp, d, scale, dst, dpl, inexact);
+    else to_lowp_kernel<2><<<g, 256, 0, st>>>(src, n, dp, d, scale, dst, dpl, inexact);
+    return cudaGetLastError();
+}
+
+}  // namespace nsg

@@ -3,6 +3,7 @@
 #include <algorithm>
 
 #include "kernels.h"
+#include "lowp.cuh"
 #include "search_core.cuh"
 
 namespace nsg {
@@ -15,38 +16,72 @@ static inline int log2i(unsigned x) {
 }
 
 struct SearchArgs {
-    const float4 *base4;
+    const float4 *base4;  // FP32 rows [n][dp4] (re-rank and the plain form)
     int dp4;
+    const uint4 *lowp;  // BF16 / FP8 rows [n][dc] 16-byte chunks (precision forms)
+    int dc;
+    float scale;  // query multiplier matching the low-precision copy
+    int rerank;   // precision forms: re-rank the final pool with FP32 rows
     const int *adj;
     int width, W;
     int start;
     const float *queries;
     int d;
     int64_t nq;
-    int k, L, H, hshift, max_steps;
+    int k, L, H, hshift, max_steps, C;
     int *ids;
     float *d2;
     int *n_expand, *n_dist, *status, *any_capped;
 };
 
-template <int G, int V, int U>
+// Alg. 1 per query.  P = PREC_F32: distances on the FP32 rows (the plain
+// form).  P = PREC_BF16 / PREC_FP8: traversal distances on the low-precision
+// copy; with `rerank` the L pool entries are then measured again on the FP32
+// rows and the k smallest of those keys are returned.
+template <int G, int V, int U, int P>
 __global__ void __launch_bounds__(256) search_kernel(SearchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const unsigned lane = lane_id();
-    WarpSmem s = carve_warp_smem(smem + warp * warp_smem_bytes(a.L, a.W, 0, a.H), a.L, a.W, 0, a.H);
+    WarpSmem s = carve_warp_smem(smem + warp * warp_smem_bytes(a.L, a.W, a.C, a.H), a.L, a.W, a.C, a.H);
     int csize = 0;
     const int64_t stride = (int64_t)gridDim.x * wpb;
     for (int64_t qi = (int64_t)blockIdx.x * wpb + warp; qi < a.nq; qi += stride) {
-        RowQuery<G, V> Q;
-        Q.load(a.queries + qi * a.d, a.d, a.dp4);
-        SearchOut o = warp_alg1<G, V, U, false, false>(Q, a.base4, a.dp4, GraphRef{a.adj, a.width},
-                                                        a.start, a.L, s, (uint32_t)a.H - 1, a.hshift,
-                                                        a.max_steps, -1, 0, csize);
+        const float *qp = a.queries + qi * a.d;
+        SearchOut o;
+        if constexpr (P == PREC_F32) {
+            DistF32<G, V, U> dist{{}, a.base4, a.dp4};
+            dist.Q.load(qp, a.d, a.dp4);
+            o = warp_alg1<false, false>(dist, GraphRef{a.adj, a.width}, a.start, a.L, s, (uint32_t)a.H - 1,
+                                        a.hshift, a.max_steps, -1, 0, csize);
+        } else {
+            constexpr int VC = (V * 4) / PrecEpc<P>::value > 0 ? (V * 4) / PrecEpc<P>::value : 1;
+            constexpr int UL = 2;
+            DistLp<P, G, VC, UL> dist{{}, a.lowp, a.dc};
+            dist.Q.load(qp, a.d, a.scale);
+            o = warp_alg1<false, false>(dist, GraphRef{a.adj, a.width}, a.start, a.L, s, (uint32_t)a.H - 1,
+                                        a.hshift, a.max_steps, -1, 0, csize);
+        }
+        const uint64_t *res = s.pool;
+        int rsize = o.size;
+        if (P != PREC_F32 && a.rerank) {
+            DistF32<G, V, U> exact{{}, a.base4, a.dp4};
+            exact.Q.load(qp, a.d, a.dp4);
+            int kept = 0;
+            for (int c0 = 0; c0 < o.size; c0 += a.W) {
+                const int mm = o.size - c0 < a.W ? o.size - c0 : a.W;
+                for (int t = lane; t < mm; t += 32) s.ids[t] = kid(s.pool[c0 + t]);
+                __syncwarp();
+                exact(s.ids, mm, s.keys);
+                warp_merge(s.clist, a.C, kept, s.keys, mm, s.ck, s.cp, s.sk, s.sp);
+            }
+            res = s.clist;
+            rsize = kept;
+        }
         for (int t = lane; t < a.k; t += 32) {
-            uint64_t e = t < o.size ? s.pool[t] : KEY_INF;
-            a.ids[qi * a.k + t] = t < o.size ? kid(e) : -1;
-            if (a.d2) a.d2[qi * a.k + t] = t < o.size ? kd2(e) : __int_as_float(0x7f800000);
+            uint64_t e = t < rsize ? res[t] : KEY_INF;
+            a.ids[qi * a.k + t] = t < rsize ? kid(e) : -1;
+            if (a.d2) a.d2[qi * a.k + t] = t < rsize ? kd2(e) : __int_as_float(0x7f800000);
         }
         if (lane == 0) {
             if (a.n_expand) a.n_expand[qi] = o.n_expand;
@@ -79,12 +114,11 @@ __global__ void __launch_bounds__(256) collect_kernel(CollectArgs a) {
     const uint32_t hmask = (uint32_t)a.H - 1;
     for (int64_t j = (int64_t)blockIdx.x * wpb + warp; j < a.nv; j += stride) {
         const int v = (int)(a.v0 + j);
-        RowQuery<G, V> Q;
-        Q.load_row(a.base4 + (int64_t)v * a.dp4, a.dp4);
+        DistF32<G, V, U> dist{{}, a.base4, a.dp4};
+        dist.Q.load_row(a.base4 + (int64_t)v * a.dp4, a.dp4);
         int csize = 0;
-        SearchOut o = warp_alg1<G, V, U, true, false>(Q, a.base4, a.dp4, GraphRef{a.knn, a.K}, a.nav,
-                                                       a.L, s, hmask, a.hshift, a.max_steps, v, a.C,
-                                                       csize);
+        SearchOut o = warp_alg1<true, false>(dist, GraphRef{a.knn, a.K}, a.nav, a.L, s, hmask, a.hshift,
+                                             a.max_steps, v, a.C, csize);
         // Alg. 2 line 7: v's nearest neighbours in G join the candidates
         const int *row = a.knn + (int64_t)v * a.K;
         int m = 0;
@@ -98,7 +132,7 @@ __global__ void __launch_bounds__(256) collect_kernel(CollectArgs a) {
         }
         __syncwarp();
         if (m > 0) {
-            rows_dist<G, V, U>(Q, a.base4, a.dp4, s.ids, m, s.keys);
+            dist(s.ids, m, s.keys);
             collect_merge(s, m, v, a.C, csize);
         }
         // Alg. 2 line 8: sorted candidates, cut to C
@@ -159,10 +193,17 @@ cudaError_t launch_search(const SearchLaunch &l, cudaStream_t st) {
     a.n_dist = l.n_dist;
     a.status = l.status;
     a.any_capped = l.any_capped;
-    size_t per_warp = warp_smem_bytes(a.L, a.W, 0, a.H);
+    a.lowp = reinterpret_cast<const uint4 *>(l.lowp);
+    a.dc = l.lowp_chunks;
+    a.scale = l.lowp_scale;
+    a.rerank = l.precision != PREC_F32 && l.rerank;
+    a.C = a.rerank ? a.k : 0;
+    size_t per_warp = warp_smem_bytes(a.L, a.W, a.C, a.H);
     cudaError_t err = cudaSuccess;
     NSG_DISPATCH_DP4(a.dp4, {
-        auto kern = search_kernel<G_, V_, U_>;
+        auto kern = l.precision == PREC_BF16  ? search_kernel<G_, V_, U_, PREC_BF16>
+                    : l.precision == PREC_FP8 ? search_kernel<G_, V_, U_, PREC_FP8>
+                                              : search_kernel<G_, V_, U_, PREC_F32>;
         int grid, wpb;
         size_t smem;
         err = config(kern, per_warp, l.warps_per_cta, l.nq, &grid, &wpb, &smem);

@@ -80,10 +80,21 @@ __device__ __forceinline__ void collect_merge(WarpSmem &s, int m, int excl, int 
     warp_merge(s.clist, C, csize, s.keys, m, s.ck, s.cp, s.sk, s.sp, excl);
 }
 
-template <int G, int V, int U, bool COLLECT, bool COHERENT>
-__device__ SearchOut warp_alg1(const RowQuery<G, V> &Q, const float4 *__restrict__ base4, int dp4,
-                               GraphRef g, int start, int L, WarpSmem &s, uint32_t hmask, int hshift,
-                               int max_steps, int excl, int C, int &csize, int *xlog = nullptr,
+// Distances of a query to FP32 rows (the plain form).
+template <int G, int V, int U>
+struct DistF32 {
+    RowQuery<G, V> Q;
+    const float4 *base4;
+    int dp4;
+    __device__ __forceinline__ void operator()(const int *ids, int m, uint64_t *keys) const {
+        rows_dist<G, V, U>(Q, base4, dp4, ids, m, keys);
+    }
+};
+
+// `dist(ids, m, keys)` writes keys[c] = (d2(query, row ids[c]), ids[c]) for c < m.
+template <bool COLLECT, bool COHERENT, class D>
+__device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, WarpSmem &s, uint32_t hmask,
+                               int hshift, int max_steps, int excl, int C, int &csize, int *xlog = nullptr,
                                int xcap = 0) {
     const unsigned lane = lane_id();
     SearchOut o;
@@ -97,7 +108,7 @@ __device__ SearchOut warp_alg1(const RowQuery<G, V> &Q, const float4 *__restrict
         s.ids[0] = start;
     }
     __syncwarp();
-    rows_dist<G, V, U>(Q, base4, dp4, s.ids, 1, s.keys);
+    dist(s.ids, 1, s.keys);
     o.n_dist = 1;
     if (lane == 0) s.pool[0] = s.keys[0];
     __syncwarp();
@@ -141,7 +152,7 @@ __device__ SearchOut warp_alg1(const RowQuery<G, V> &Q, const float4 *__restrict
             cursor = i + 1;
             continue;
         }
-        rows_dist<G, V, U>(Q, base4, dp4, s.ids, m, s.keys);
+        dist(s.ids, m, s.keys);
         o.n_dist += m;
         if (COLLECT) collect_merge(s, m, excl, C, csize);
         int lo = warp_merge(s.pool, L, o.size, s.keys, m, s.ck, s.cp, s.sk, s.sp);
