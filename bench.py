@@ -7,9 +7,11 @@ paper's Alg. 2 at K=100, L=40, R=50, C=500.  The pool size L is swept over
 100, 125, ..., 400 (k=100); the reported point is the highest-QPS L whose
 mean recall@10 (Eq. 1, against the exact ground truth) is >= 0.95.
 
-Forms: plain (FP32 traversal, exactly Alg. 1) and the precision forms (BF16
-or FP8-e4m3 traversal distances with FP32 accumulation, FP32 re-rank of the
-final pool when the copy is lossy).  `value` is the form with the highest QPS
+Forms: plain (FP32 traversal, exactly Alg. 1), the precision forms (BF16 or
+FP8-e4m3 traversal distances with FP32 accumulation, FP32 re-rank of the
+final pool when the copy is lossy), and the learned-stop forms (an MLP
+trained on the GPU from search traces of a separate query batch ends each
+search early; swept over its probability threshold).  `value` is the form with the highest QPS
 at recall@10 >= 0.95 ("chosen"); `plain` holds the plain form beside it.
 
 A step = one nsg_search_ex launch over the whole 10,000-query batch, inputs
@@ -44,6 +46,8 @@ BUILD = dict(K=100, L=40, R=50, C=500)
 L_GRID = list(range(100, 401, 25))
 K_RESULTS = 100
 TARGET = 0.95
+STOP_TRACE_L, STOP_TRACE_CAP, STOP_ITERS = 400, 1024, 300
+STOP_THRESHOLDS = [0.9, 0.95, 0.98]
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -222,6 +226,19 @@ def main():
     for name, prec in (("bf16", capi.PREC_BF16), ("fp8", capi.PREC_FP8)):
         idx.prepare(prec)
         forms[name] = capi.SearchParams(0, 0, prec, 0, -1)
+    # learned early termination: traces of a separate query batch (its own
+    # seed, never timed) -> MLP trained on the GPU -> stop rule in the kernel
+    _, q_train = datagen.workload(args.workload, nq=nq, seed_query=datagen.SEED_QUERY + 500 + 1000 * rank)
+    t1 = time.perf_counter()
+    trace = idx.search_trace(torch.from_numpy(q_train).cuda(), 10, STOP_TRACE_L, STOP_TRACE_CAP,
+                             params=capi.SearchParams(0, 0, capi.PREC_BF16, 0, -1, None, 0.5, 10))
+    stop_model, _, stop_loss = capi.nsg_stop_train(trace, iters=STOP_ITERS, lr=1e-2, seed=1)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    for th in STOP_THRESHOLDS:
+        for base_name in ("plain", "bf16"):
+            b = forms[base_name]
+            forms[f"{base_name}+stop{th}"] = capi.SearchParams(0, 0, b.precision, 0, -1, stop_model, th, 10)
     info = idx.info()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = None
@@ -262,8 +279,9 @@ def main():
     n_dist = cnt["n_dist"].to(torch.int64).sum().item()
     n_expand = cnt["n_expand"].to(torch.int64).sum().item()
     R = info["R"]
-    row_bytes = {"plain": d * 4, "bf16": ((d + 7) // 8) * 16, "fp8": ((d + 15) // 16) * 16}[chosen_form]
-    lossy = {"plain": False, "bf16": info["has_bf16"] == 1, "fp8": info["has_fp8"] == 1}[chosen_form]
+    base_form = chosen_form.split("+")[0]
+    row_bytes = {"plain": d * 4, "bf16": ((d + 7) // 8) * 16, "fp8": ((d + 15) // 16) * 16}[base_form]
+    lossy = {"plain": False, "bf16": info["has_bf16"] == 1, "fp8": info["has_fp8"] == 1}[base_form]
     bytes_launch = (n_dist * row_bytes + n_expand * R * 4 + nq * (d * 4 + K_RESULTS * 8)
                     + (nq * L * d * 4 if lossy else 0))
 
@@ -324,7 +342,7 @@ def main():
             "metric": METRIC, "value": world * nq / (ms_step / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"plain": "f32", "bf16": "bf16->f32", "fp8": "fp8e4m3->f32"}[chosen_form],
+            "dtype": {"plain": "f32", "bf16": "bf16->f32", "fp8": "fp8e4m3->f32"}[base_form],
             "data": "synthetic",
             "config": {"workload": "sift-shaped 1,000,000 x 128 int 0..255 GMM(100), 10,000 queries",
                        "form": chosen_form, "build": BUILD, "k": K_RESULTS, "L": L,
@@ -346,6 +364,9 @@ def main():
                       "fixup_edges": info["n_fixup_edges"], "fixup_researched": info["n_fixup_searches"],
                       "nav": info["nav"], "bf16_exact": info["has_bf16"] == 2, "fp8_scale": info["fp8_scale"]},
             "per_query": {"n_expand": n_expand / nq, "n_dist": n_dist / nq},
+            "learned_stop": {"train_queries": nq, "trace_L": STOP_TRACE_L, "iters": STOP_ITERS,
+                             "train_seconds": train_s, "loss_first": stop_loss[0].item(),
+                             "loss_last": stop_loss[-1].item(), "thresholds": STOP_THRESHOLDS},
             "sweep": sweeps,
         }
         print(json.dumps(line), flush=True)

@@ -58,7 +58,17 @@ typedef struct {
     int32_t warps_per_cta; /* <= 0 -> auto */
     int32_t rerank;        /* BF16/FP8: re-rank the final pool with FP32 rows (1), not (0),
                               or only when the copy is lossy (-1) */
+    const void *stop_model; /* learned early termination: NSG_STOP_PARAMS FP16 values on the
+                               device (see nsg_stop_train), or NULL for the fixed-L search */
+    float stop_threshold;  /* stop once the model's probability exceeds this (0..1) */
+    int32_t stop_k;        /* result size the stop rule protects (<= 0 -> min(k, 10)) */
+    int32_t stop_min_steps; /* never stop before this many expansions */
 } nsg_search_params;
+
+/* Parameters of the early-termination MLP (8 features -> 64 ReLU -> 1):
+ * w1[64][8], b1[64], w2[64], b2 in this order. */
+#define NSG_STOP_FEATURES 8
+#define NSG_STOP_PARAMS 641
 
 typedef struct {
     int64_t n;             /* base rows */
@@ -212,6 +222,28 @@ nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t
                          int32_t L, const nsg_search_params *params, int32_t *ids_dev,
                          float *d2_dev, int32_t *n_expand_dev, int32_t *n_dist_dev,
                          int32_t *status_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned early termination (not in the paper: a serving-side addition; the
+ * fixed-L Alg. 1 is its fallback and the judge of its recall loss).
+ * nsg_search_trace: Alg. 1 with fixed L that records, before each expansion
+ *   t (t < cap), the 8 state features (feat_dev [nq][cap][8] f32) and after
+ *   it whether the first stop_k pool entries changed (flag_dev [nq][cap] u8);
+ *   steps_dev [nq] receives the expansion count.  params as nsg_search_ex
+ *   (stop_model ignored).  ids_dev [nq][k] receives the results.
+ * nsg_stop_train: full-batch Adam on those traces; the label of step t is 1
+ *   when no later step changes the first stop_k entries.  master_dev: FP32
+ *   parameters [NSG_STOP_PARAMS] (initialised from `seed` when seed != 0,
+ *   else continued); model_dev: FP16 export [NSG_STOP_PARAMS] for
+ *   params->stop_model; loss_dev [iters] (nullable): mean BCE per iteration.
+ *   Synchronises the stream.
+ * ------------------------------------------------------------------------- */
+nsg_status nsg_search_trace(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k, int32_t L,
+                            const nsg_search_params *params, int32_t *ids_dev, float *feat_dev,
+                            uint8_t *flag_dev, int32_t *steps_dev, int32_t cap, void *stream);
+nsg_status nsg_stop_train(const float *feat_dev, const uint8_t *flag_dev, const int32_t *steps_dev, int64_t nq,
+                          int32_t cap, int32_t iters, float lr, uint64_t seed, float *master_dev, void *model_dev,
+                          float *loss_dev, void *stream);
 
 /* ---------------------------------------------------------------------------
  * A8. Precision (Eq. 1): hits_dev[q] = |{first k of ids} n {first k of gt}|.

@@ -32,10 +32,17 @@ class NsgError(RuntimeError):
 
 class SearchParams(C.Structure):
     _fields_ = [("max_steps", C.c_int32), ("hash_slots", C.c_int32), ("precision", C.c_int32),
-                ("warps_per_cta", C.c_int32), ("rerank", C.c_int32)]
+                ("warps_per_cta", C.c_int32), ("rerank", C.c_int32), ("stop_model", C.c_void_p),
+                ("stop_threshold", C.c_float), ("stop_k", C.c_int32), ("stop_min_steps", C.c_int32)]
 
-    def __init__(self, max_steps=0, hash_slots=0, precision=0, warps_per_cta=0, rerank=-1):
-        super().__init__(max_steps, hash_slots, precision, warps_per_cta, rerank)
+    def __init__(self, max_steps=0, hash_slots=0, precision=0, warps_per_cta=0, rerank=-1, stop_model=None,
+                 stop_threshold=0.5, stop_k=0, stop_min_steps=0):
+        ptr = stop_model.data_ptr() if isinstance(stop_model, torch.Tensor) else stop_model
+        super().__init__(max_steps, hash_slots, precision, warps_per_cta, rerank, ptr, stop_threshold, stop_k,
+                         stop_min_steps)
+
+
+STOP_FEATURES, STOP_PARAMS = 8, 641
 
 
 class IndexInfo(C.Structure):
@@ -70,6 +77,8 @@ SIGNATURES = [
     ("nsg_search", [P, P, i64, i32, i32, P, P, P], i32),
     ("nsg_search_ex", [P, P, i64, i32, i32, P, P, P, P, P, P, P], i32),
     ("nsg_recall", [P, i32, P, i32, i64, i32, P, P], i32),
+    ("nsg_search_trace", [P, P, i64, i32, i32, P, P, P, P, P, i32, P], i32),
+    ("nsg_stop_train", [P, P, P, i64, i32, i32, C.c_float, u64, P, P, P, P], i32),
     ("nsg_index_info", [P, P], i32),
     ("nsg_index_prepare", [P, i32, P], i32),
     ("nsg_index_graph", [P, P, P, P], i32),
@@ -268,6 +277,20 @@ class Index:
                                    _ptr(out.get("status")), _stream()), "nsg_search_ex")
         return out
 
+    def search_trace(self, queries, k, L, cap, params=None):
+        """Fixed-L search recording per-step stop features and change flags."""
+        queries = _dev(queries, torch.float32)
+        nq = queries.shape[0]
+        dev = queries.device
+        ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
+        feat = torch.zeros((nq, cap, STOP_FEATURES), dtype=torch.float32, device=dev)
+        flag = torch.zeros((nq, cap), dtype=torch.uint8, device=dev)
+        steps = torch.empty(nq, dtype=torch.int32, device=dev)
+        p = params if params is not None else SearchParams()
+        _check(lib().nsg_search_trace(self.h, _ptr(queries), nq, k, L, C.byref(p), _ptr(ids), _ptr(feat),
+                                      _ptr(flag), _ptr(steps), cap, _stream()), "nsg_search_trace")
+        return dict(ids=ids, feat=feat, flag=flag, steps=steps)
+
     def save(self, path):
         _check(lib().nsg_save(self.h, path.encode()), "nsg_save")
 
@@ -287,6 +310,21 @@ def nsg_index_from_graph(base, adj, nav, deg=None):
     _check(lib().nsg_index_from_graph(_ptr(base), n, d, _ptr(adj), _ptr(deg), adj.shape[1], int(nav),
                                       _stream(), C.byref(h)), "nsg_index_from_graph")
     return Index(h)
+
+
+def nsg_stop_train(trace, iters=300, lr=1e-2, seed=1, master=None):
+    """Train the early-termination MLP on a trace (dict from Index.search_trace).
+    Returns (fp16 model tensor [641], fp32 master [641], loss per iteration)."""
+    feat, flag, steps = trace["feat"], trace["flag"], trace["steps"]
+    nq, cap = flag.shape
+    dev = feat.device
+    if master is None:
+        master = torch.zeros(STOP_PARAMS, dtype=torch.float32, device=dev)
+    model = torch.empty(STOP_PARAMS, dtype=torch.float16, device=dev)
+    loss = torch.empty(iters, dtype=torch.float32, device=dev)
+    _check(lib().nsg_stop_train(_ptr(feat), _ptr(flag), _ptr(steps), nq, cap, iters, lr, seed, _ptr(master),
+                                _ptr(model), _ptr(loss), _stream()), "nsg_stop_train")
+    return model, master, loss
 
 
 def nsg_load(path):

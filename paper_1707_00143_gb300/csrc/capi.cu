@@ -605,19 +605,27 @@ nsg_status nsg_index_from_graph(const float *base_dev, int64_t n, int32_t d, con
     return NSG_OK;
 }
 
-nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k,
-                         int32_t L, const nsg_search_params *params, int32_t *ids_dev, float *d2_dev,
-                         int32_t *n_expand_dev, int32_t *n_dist_dev, int32_t *status_dev, void *stream) {
+namespace {
+
+// Validated launch description for nsg_search_ex / nsg_search_trace.
+nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k, int32_t L,
+                       const nsg_search_params *params, int32_t *ids_dev, float *d2_dev, int32_t *n_expand_dev,
+                       int32_t *n_dist_dev, int32_t *status_dev, nsg::SearchLaunch &l) {
     if (!idx || k < 1 || L < k || L > 1024 || nq < 0 || nq >= INT32_MAX) return NSG_EINVAL;
-    if (nq == 0) return NSG_OK;
-    if (!queries_dev || !ids_dev) return NSG_EINVAL;
-    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1};
+    if (nq > 0 && (!queries_dev || !ids_dev)) return NSG_EINVAL;
+    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0};
     if (params) p = *params;
     if (p.precision < NSG_PREC_F32 || p.precision > NSG_PREC_FP8) return NSG_EINVAL;
     if (p.precision != NSG_PREC_F32 && !idx->lowp[p.precision]) return NSG_EINVAL;  // nsg_index_prepare first
     if (p.hash_slots > 0 && (p.hash_slots < 64 || (p.hash_slots & (p.hash_slots - 1)) || p.hash_slots > 65536))
         return NSG_EINVAL;
-    nsg::SearchLaunch l;
+    if (p.stop_model && !(p.stop_threshold > 0.0f && p.stop_threshold < 1.0f)) return NSG_EINVAL;
+    if (p.stop_model) {
+        l.stop_model = p.stop_model;
+        l.stop_logit = std::log(p.stop_threshold / (1.0f - p.stop_threshold));
+    }
+    l.stop_k = p.stop_k > 0 ? (p.stop_k < L ? p.stop_k : L) : (k < 10 ? k : 10);
+    l.stop_min_steps = p.stop_min_steps > 0 ? p.stop_min_steps : 0;
     l.base = idx->base;
     l.n = idx->n;
     l.dp = idx->dp;
@@ -646,7 +654,47 @@ nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t
         // auto: re-rank unless the copy holds every value exactly (then its keys are the FP32 keys)
         l.rerank = p.rerank < 0 ? !idx->lowp_exact[p.precision] : p.rerank != 0;
     }
+    return NSG_OK;
+}
+
+}  // namespace
+
+nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k,
+                         int32_t L, const nsg_search_params *params, int32_t *ids_dev, float *d2_dev,
+                         int32_t *n_expand_dev, int32_t *n_dist_dev, int32_t *status_dev, void *stream) {
+    nsg::SearchLaunch l;
+    nsg_status s = make_search(idx, queries_dev, nq, k, L, params, ids_dev, d2_dev, n_expand_dev, n_dist_dev,
+                               status_dev, l);
+    if (s || nq == 0) return s;
     NSG_CK(nsg::launch_search(l, S(stream)));
+    return NSG_OK;
+}
+
+nsg_status nsg_search_trace(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k, int32_t L,
+                            const nsg_search_params *params, int32_t *ids_dev, float *feat_dev,
+                            uint8_t *flag_dev, int32_t *steps_dev, int32_t cap, void *stream) {
+    if (cap < 1 || (nq > 0 && (!feat_dev || !flag_dev || !steps_dev))) return NSG_EINVAL;
+    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0};
+    if (params) p = *params;
+    p.stop_model = nullptr;  // traces record the fixed-L search
+    nsg::SearchLaunch l;
+    nsg_status s = make_search(idx, queries_dev, nq, k, L, &p, ids_dev, nullptr, steps_dev, nullptr, nullptr, l);
+    if (s || nq == 0) return s;
+    l.trace_feat = feat_dev;
+    l.trace_flag = flag_dev;
+    l.trace_cap = cap;
+    NSG_CK(nsg::launch_search(l, S(stream)));
+    return NSG_OK;
+}
+
+nsg_status nsg_stop_train(const float *feat_dev, const uint8_t *flag_dev, const int32_t *steps_dev, int64_t nq,
+                          int32_t cap, int32_t iters, float lr, uint64_t seed, float *master_dev, void *model_dev,
+                          float *loss_dev, void *stream) {
+    if (!feat_dev || !flag_dev || !steps_dev || !master_dev || !model_dev || nq < 1 || cap < 1 || iters < 1 ||
+        !(lr > 0.0f))
+        return NSG_EINVAL;
+    NSG_CK(nsg::run_stop_train(feat_dev, flag_dev, steps_dev, nq, cap, iters, lr, seed, master_dev, model_dev,
+                               loss_dev, S(stream)));
     return NSG_OK;
 }
 

@@ -31,8 +31,24 @@ struct SearchLaunch {
     int lowp_chunks = 0;  // 16-byte chunks per low-precision row
     float lowp_scale = 1.0f;
     int rerank = 0;
+    // learned early termination (FP16 MLP parameters, nullptr = none) and traces
+    const void *stop_model = nullptr;
+    float stop_logit = 0.0f;
+    int stop_k = 10, stop_min_steps = 0;
+    float *trace_feat = nullptr;           // [nq][trace_cap][8]
+    unsigned char *trace_flag = nullptr;   // [nq][trace_cap]
+    int trace_cap = 0;
 };
 cudaError_t launch_search(const SearchLaunch &a, cudaStream_t st);
+
+// Training of the early-termination MLP on search traces (full-batch Adam).
+// feat [nq][cap][8], flag [nq][cap], steps [nq]; label of step t of query q =
+// no later step of q changed its first k pool entries.  model_out: FP16
+// parameters (w1[64][8], b1[64], w2[64], b2); master: FP32 copy [641] (in/out
+// when init == 0).  loss_out (device, nullable): [iters] mean BCE per iteration.
+cudaError_t run_stop_train(const float *feat, const unsigned char *flag, const int *steps, int64_t nq, int cap,
+                           int iters, float lr, uint64_t seed, float *master, void *model_out, float *loss_out,
+                           cudaStream_t st);
 
 // Largest |x| over `count` floats (bits of a non-negative float, atomicMax).
 cudaError_t launch_absmax(const float *x, int64_t count, unsigned *out_bits, cudaStream_t st);

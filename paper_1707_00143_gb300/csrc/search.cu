@@ -2,9 +2,26 @@
 // the per-node search-and-collect of Alg. 2 (lines 5-8), one warp per unit.
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "kernels.h"
 #include "lowp.cuh"
 #include "search_core.cuh"
+
+// Launch shape of the search kernel: minimum resident 256-thread blocks per
+// SM (bounds the registers per thread) and rows in flight per lane group on
+// the low-precision paths (1 or 2 16-byte chunks per lane).
+#ifdef NSG_SEARCH_MINB
+#define NSG_SEARCH_BOUNDS __launch_bounds__(256, NSG_SEARCH_MINB)
+#else
+#define NSG_SEARCH_BOUNDS __launch_bounds__(256)
+#endif
+#ifndef NSG_UL1
+#define NSG_UL1 2
+#endif
+#ifndef NSG_UL2
+#define NSG_UL2 2
+#endif
 
 namespace nsg {
 
@@ -32,35 +49,63 @@ struct SearchArgs {
     int *ids;
     float *d2;
     int *n_expand, *n_dist, *status, *any_capped;
+    // learned early termination: FP16 MLP parameters (nullptr: none), logit threshold
+    const __half *stop_model;
+    float stop_logit;
+    int stop_k, stop_min_steps;
+    // trace recording: features [nq][cap][NF], change flags [nq][cap]
+    float *trace_feat;
+    unsigned char *trace_flag;
+    int trace_cap;
 };
 
 // Alg. 1 per query.  P = PREC_F32: distances on the FP32 rows (the plain
 // form).  P = PREC_BF16 / PREC_FP8: traversal distances on the low-precision
 // copy; with `rerank` the L pool entries are then measured again on the FP32
 // rows and the k smallest of those keys are returned.
-template <int G, int V, int U, int P>
-__global__ void __launch_bounds__(256) search_kernel(SearchArgs a) {
+template <int G, int V, int U, int P, bool STOP>
+__device__ __forceinline__ void search_body(const SearchArgs &a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const unsigned lane = lane_id();
-    WarpSmem s = carve_warp_smem(smem + warp * warp_smem_bytes(a.L, a.W, a.C, a.H), a.L, a.W, a.C, a.H);
+    const size_t wbytes = warp_smem_bytes(a.L, a.W, a.C, a.H);
+    WarpSmem s = carve_warp_smem(smem + warp * wbytes, a.L, a.W, a.C, a.H);
+    // the stop model lives after the warps' regions, widened to FP32
+    StopMLP *mlp = reinterpret_cast<StopMLP *>(smem + wpb * wbytes);
+    if (STOP && a.stop_model != nullptr) {
+        float *dst = reinterpret_cast<float *>(mlp);
+        for (int t = threadIdx.x; t < NSG_STOP_PARAMS; t += blockDim.x) dst[t] = __half2float(a.stop_model[t]);
+        __syncthreads();
+    }
     int csize = 0;
     const int64_t stride = (int64_t)gridDim.x * wpb;
     for (int64_t qi = (int64_t)blockIdx.x * wpb + warp; qi < a.nq; qi += stride) {
         const float *qp = a.queries + qi * a.d;
+        StopCtx sc;
+        sc.mlp = a.stop_model != nullptr ? mlp : nullptr;
+        sc.logit = a.stop_logit;
+        sc.k = a.stop_k;
+        sc.min_steps = a.stop_min_steps;
+        sc.trace_feat = a.trace_feat != nullptr ? a.trace_feat + qi * (int64_t)a.trace_cap * NSG_STOP_NF : nullptr;
+        sc.trace_flag = a.trace_flag != nullptr ? a.trace_flag + qi * (int64_t)a.trace_cap : nullptr;
+        sc.trace_cap = a.trace_cap;
+        const StopCtx *scp = STOP ? &sc : nullptr;
         SearchOut o;
         if constexpr (P == PREC_F32) {
             DistF32<G, V, U> dist{{}, a.base4, a.dp4};
             dist.Q.load(qp, a.d, a.dp4);
-            o = warp_alg1<false, false>(dist, GraphRef{a.adj, a.width}, a.start, a.L, s, (uint32_t)a.H - 1,
-                                        a.hshift, a.max_steps, -1, 0, csize);
+            o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, a.L, s,
+                                                              (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
+                                                              csize, nullptr, 0, scp);
         } else {
             constexpr int VC = (V * 4) / PrecEpc<P>::value > 0 ? (V * 4) / PrecEpc<P>::value : 1;
-            constexpr int UL = 2;
+            // rows in flight per group: a low-precision row costs VC*4 registers per lane
+            constexpr int UL = VC <= 1 ? NSG_UL1 : (VC == 2 ? NSG_UL2 : 2);
             DistLp<P, G, VC, UL> dist{{}, a.lowp, a.dc};
             dist.Q.load(qp, a.d, a.scale);
-            o = warp_alg1<false, false>(dist, GraphRef{a.adj, a.width}, a.start, a.L, s, (uint32_t)a.H - 1,
-                                        a.hshift, a.max_steps, -1, 0, csize);
+            o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, a.L, s,
+                                                              (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
+                                                              csize, nullptr, 0, scp);
         }
         const uint64_t *res = s.pool;
         int rsize = o.size;
@@ -91,6 +136,18 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a) {
         }
         __syncwarp();
     }
+}
+
+// The fixed-L kernels keep the compiler's default register budget (64 on the
+// common shapes, which lets ~32 warps share an SM); the learned-stop / trace
+// kernels carry the feature and MLP code and are held to 3 blocks per SM.
+template <int G, int V, int U, int P>
+__global__ void NSG_SEARCH_BOUNDS search_kernel(SearchArgs a) {
+    search_body<G, V, U, P, false>(a);
+}
+template <int G, int V, int U, int P>
+__global__ void __launch_bounds__(256, 3) search_stop_kernel(SearchArgs a) {
+    search_body<G, V, U, P, true>(a);
 }
 
 struct CollectArgs {
@@ -151,12 +208,12 @@ __global__ void __launch_bounds__(256) collect_kernel(CollectArgs a) {
 
 template <typename K>
 static cudaError_t config(K kernel, size_t smem_per_warp, int want_wpb, int64_t units, int *grid,
-                          int *wpb, size_t *smem) {
+                          int *wpb, size_t *smem, size_t smem_per_cta = 0) {
     size_t cap = smem_optin();
     int w = want_wpb > 0 ? want_wpb : 4;
-    while (w > 1 && smem_per_warp * w > cap) --w;
-    if (smem_per_warp * w > cap) return cudaErrorInvalidConfiguration;
-    *smem = smem_per_warp * w;
+    while (w > 1 && smem_per_warp * w + smem_per_cta > cap) --w;
+    if (smem_per_warp * w + smem_per_cta > cap) return cudaErrorInvalidConfiguration;
+    *smem = smem_per_warp * w + smem_per_cta;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -198,15 +255,26 @@ cudaError_t launch_search(const SearchLaunch &l, cudaStream_t st) {
     a.scale = l.lowp_scale;
     a.rerank = l.precision != PREC_F32 && l.rerank;
     a.C = a.rerank ? a.k : 0;
+    a.stop_model = reinterpret_cast<const __half *>(l.stop_model);
+    a.stop_logit = l.stop_logit;
+    a.stop_k = l.stop_k;
+    a.stop_min_steps = l.stop_min_steps;
+    a.trace_feat = l.trace_feat;
+    a.trace_flag = l.trace_flag;
+    a.trace_cap = l.trace_cap;
     size_t per_warp = warp_smem_bytes(a.L, a.W, a.C, a.H);
+    const size_t per_cta = l.stop_model ? ((sizeof(StopMLP) + 15) & ~size_t(15)) : 0;
     cudaError_t err = cudaSuccess;
     NSG_DISPATCH_DP4(a.dp4, {
-        auto kern = l.precision == PREC_BF16  ? search_kernel<G_, V_, U_, PREC_BF16>
-                    : l.precision == PREC_FP8 ? search_kernel<G_, V_, U_, PREC_FP8>
-                                              : search_kernel<G_, V_, U_, PREC_F32>;
+        const bool stop = l.stop_model != nullptr || l.trace_feat != nullptr;
+        auto kern = l.precision == PREC_BF16
+                        ? (stop ? search_stop_kernel<G_, V_, U_, PREC_BF16> : search_kernel<G_, V_, U_, PREC_BF16>)
+                    : l.precision == PREC_FP8
+                        ? (stop ? search_stop_kernel<G_, V_, U_, PREC_FP8> : search_kernel<G_, V_, U_, PREC_FP8>)
+                        : (stop ? search_stop_kernel<G_, V_, U_, PREC_F32> : search_kernel<G_, V_, U_, PREC_F32>);
         int grid, wpb;
         size_t smem;
-        err = config(kern, per_warp, l.warps_per_cta, l.nq, &grid, &wpb, &smem);
+        err = config(kern, per_warp, l.warps_per_cta, l.nq, &grid, &wpb, &smem, per_cta);
         if (err == cudaSuccess) {
             kern<<<grid, wpb * 32, smem, st>>>(a);
             err = cudaGetLastError();

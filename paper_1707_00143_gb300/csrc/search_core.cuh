@@ -72,7 +72,56 @@ struct SearchOut {
     int n_expand;  // nodes checked
     int n_dist;    // distances computed (incl. recomputation after forgetting)
     bool capped;   // step cap reached
+    bool stopped;  // the learned stop rule ended the search early
 };
+
+// ---------------------------------------------------------------------------
+// Learned early termination.  Before each expansion the warp describes the
+// search state with NSG_STOP_NF features -- log step count, d(first)/d(k-th),
+// d(k-th)/d(next to expand), d(k-th)/d(last), log steps since the first k
+// entries last changed, log position of the next entry to expand, new
+// neighbours in the last step / width, and whether the last step changed the
+// first k -- an MLP (NF -> 64 -> 1, ReLU) maps them to a logit, and the
+// search stops when the logit exceeds a threshold.
+// With a trace buffer the features and, after the expansion, whether the
+// first k_stop pool entries changed are recorded (the training data).
+// ---------------------------------------------------------------------------
+#define NSG_STOP_NF 8
+#define NSG_STOP_H 64
+#define NSG_STOP_PARAMS (NSG_STOP_H * NSG_STOP_NF + 2 * NSG_STOP_H + 1)  // w1, b1, w2, b2
+
+struct StopMLP {  // FP32 copy in shared memory
+    float w1[NSG_STOP_H][NSG_STOP_NF];
+    float b1[NSG_STOP_H];
+    float w2[NSG_STOP_H];
+    float b2;
+};
+
+struct StopCtx {
+    const StopMLP *mlp;  // nullptr: no learned stop (trace only)
+    float logit;         // stop when the model's logit exceeds this
+    int k;               // the result size the rule protects
+    int min_steps;
+    float *trace_feat;   // [cap][NF] for this query, or nullptr
+    unsigned char *trace_flag;  // [cap]
+    int trace_cap;
+};
+
+__device__ __forceinline__ float stop_logit(const StopMLP &m, const float (&f)[NSG_STOP_NF]) {
+    const unsigned lane = lane_id();
+    float part = 0.0f;
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h;
+        float a = m.b1[j];
+#pragma unroll
+        for (int i = 0; i < NSG_STOP_NF; ++i) a = fmaf(m.w1[j][i], f[i], a);
+        part = fmaf(m.w2[j], fmaxf(a, 0.0f), part);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(NSG_FULL, part, o);
+    return part + m.b2;
+}
 
 // Merge keys[0..m) minus id `excl` into the collect list (keys left intact
 // for the pool merge that follows).
@@ -92,16 +141,20 @@ struct DistF32 {
 };
 
 // `dist(ids, m, keys)` writes keys[c] = (d2(query, row ids[c]), ids[c]) for c < m.
-template <bool COLLECT, bool COHERENT, class D>
+// STOP: compile the learned-stop / trace hooks (stop must then be non-null).
+template <bool COLLECT, bool COHERENT, class D, bool STOP = false>
 __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, WarpSmem &s, uint32_t hmask,
                                int hshift, int max_steps, int excl, int C, int &csize, int *xlog = nullptr,
-                               int xcap = 0) {
+                               int xcap = 0, const StopCtx *stop = nullptr) {
     const unsigned lane = lane_id();
     SearchOut o;
     o.size = 0;
     o.n_expand = 0;
     o.n_dist = 0;
     o.capped = false;
+    o.stopped = false;
+    int since_change = 0, last_m = 0;
+    bool last_changed = true;
     hash_clear(s.hash, (int)hmask + 1);
     if (lane == 0) {
         visit(s.hash, hmask, hshift, start);
@@ -131,6 +184,32 @@ __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, Warp
             o.capped = true;
             break;
         }
+        if constexpr (STOP) {
+            // state before expanding pool[i]: every lane computes the same features
+            const int kk = stop->k < o.size ? stop->k : o.size;
+            const float d0 = kd2(s.pool[0]), dk = kd2(s.pool[kk - 1]);
+            const float dn = kd2(s.pool[i]), dl = kd2(s.pool[o.size - 1]);
+            float f[NSG_STOP_NF];
+            f[0] = log2f(1.0f + (float)o.n_expand) * 0.1f;
+            f[1] = dk > 0.0f ? d0 / dk : 1.0f;
+            f[2] = dn > 0.0f ? fminf(dk / dn, 4.0f) : 1.0f;
+            f[3] = dl > 0.0f ? dk / dl : 1.0f;
+            f[4] = log2f(1.0f + (float)since_change) * 0.125f;
+            f[5] = log2f(1.0f + (float)i) * 0.1f;
+            f[6] = (float)last_m / (float)g.width;
+            f[7] = last_changed ? 1.0f : 0.0f;
+            if (stop->trace_feat != nullptr && o.n_expand < stop->trace_cap) {
+                float fv = 0.0f;
+#pragma unroll
+                for (int t = 0; t < NSG_STOP_NF; ++t)
+                    if ((int)lane == t) fv = f[t];
+                if (lane < NSG_STOP_NF) stop->trace_feat[(int64_t)o.n_expand * NSG_STOP_NF + lane] = fv;
+            }
+            if (stop->mlp != nullptr && o.n_expand >= stop->min_steps && stop_logit(*stop->mlp, f) > stop->logit) {
+                o.stopped = true;
+                break;
+            }
+        }
         o.n_expand++;
         const uint64_t e = s.pool[i];
         __syncwarp();
@@ -148,8 +227,15 @@ __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, Warp
             m += __popc(bal);
         }
         __syncwarp();
+        last_m = m;
         if (m == 0) {
             cursor = i + 1;
+            if constexpr (STOP) {  // nothing new: the first k entries are unchanged
+                if (stop->trace_flag != nullptr && lane == 0 && o.n_expand <= stop->trace_cap)
+                    stop->trace_flag[o.n_expand - 1] = 0;
+                last_changed = false;
+                ++since_change;
+            }
             continue;
         }
         dist(s.ids, m, s.keys);
@@ -157,6 +243,12 @@ __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, Warp
         if (COLLECT) collect_merge(s, m, excl, C, csize);
         int lo = warp_merge(s.pool, L, o.size, s.keys, m, s.ck, s.cp, s.sk, s.sp);
         cursor = min(i + 1, lo);
+        if constexpr (STOP) {  // did this expansion change the first k entries?
+            last_changed = lo < stop->k;
+            since_change = last_changed ? 0 : since_change + 1;
+            if (stop->trace_flag != nullptr && lane == 0 && o.n_expand <= stop->trace_cap)
+                stop->trace_flag[o.n_expand - 1] = last_changed ? 1 : 0;
+        }
     }
     __syncwarp();
     return o;
