@@ -46,8 +46,8 @@ BUILD = dict(K=100, L=40, R=50, C=500)
 L_GRID = list(range(100, 401, 25))
 K_RESULTS = 100
 TARGET = 0.95
-STOP_TRACE_L, STOP_TRACE_CAP, STOP_ITERS = 400, 1024, 300
-STOP_THRESHOLDS = [0.9, 0.95, 0.98]
+STOP_TRACE_L, STOP_TRACE_CAP, STOP_ITERS = 250, 1024, 300
+STOP_THRESHOLDS = [0.5, 0.7, 0.9]
 FALLBACK_HBM_GBS = 6800.0
 
 

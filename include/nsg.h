@@ -224,6 +224,41 @@ nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t
                          int32_t *status_dev, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched uneven queries (not in the paper: a serving-side addition).  Query
+ *   q asks for k_dev[q] results with pool L_dev[q] (clamped to 1..kmax and
+ *   max(k_q, .)..Lmax).  Outputs are [nq][kmax] rows, padded with -1 / +inf
+ *   past each query's k.  One persistent launch: warps draw queries from a
+ *   device work counter, longest pool first.
+ * nsg_search_batched: one-shot form (derives the visiting order each call).
+ * nsg_plan_create: binds an index, the query / k / L / output buffers and
+ *   the parameters; derives the visiting order; with `autotune` times the
+ *   candidate launch shapes (warps per block 2/4/8 x visited-hash slots
+ *   512/1024/2048) on the bound batch and keeps the fastest; then captures
+ *   "reset work counter + search" as a CUDA graph.  Synchronises.
+ * nsg_plan_run: replays the graph on `stream` (asynchronous).
+ * nsg_plan_info: the chosen shape and the tuning timings.
+ * ------------------------------------------------------------------------- */
+typedef struct nsg_plan nsg_plan;
+typedef struct {
+    int32_t warps_per_cta; /* chosen launch shape */
+    int32_t hash_slots;
+    int32_t n_tried;       /* shapes timed by the autotuner (0: none) */
+    float best_ms;         /* time of one run of the chosen shape (autotune only) */
+    float worst_ms;        /* slowest shape tried */
+} nsg_plan_info_t;
+
+nsg_status nsg_search_batched(const nsg_index *idx, const float *queries_dev, int64_t nq, const int32_t *k_dev,
+                              const int32_t *L_dev, int32_t kmax, int32_t Lmax, const nsg_search_params *params,
+                              int32_t *ids_dev, float *d2_dev, int32_t *status_dev, void *stream);
+nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64_t nq, const int32_t *k_dev,
+                           const int32_t *L_dev, int32_t kmax, int32_t Lmax, const nsg_search_params *params,
+                           int32_t *ids_dev, float *d2_dev, int32_t *status_dev, int32_t autotune, void *stream,
+                           nsg_plan **out);
+nsg_status nsg_plan_run(nsg_plan *plan, void *stream);
+nsg_status nsg_plan_info(const nsg_plan *plan, nsg_plan_info_t *info);
+void nsg_plan_free(nsg_plan *plan);
+
+/* ---------------------------------------------------------------------------
  * Learned early termination (not in the paper: a serving-side addition; the
  * fixed-L Alg. 1 is its fallback and the judge of its recall loss).
  * nsg_search_trace: Alg. 1 with fixed L that records, before each expansion

@@ -78,6 +78,11 @@ SIGNATURES = [
     ("nsg_search_ex", [P, P, i64, i32, i32, P, P, P, P, P, P, P], i32),
     ("nsg_recall", [P, i32, P, i32, i64, i32, P, P], i32),
     ("nsg_search_trace", [P, P, i64, i32, i32, P, P, P, P, P, i32, P], i32),
+    ("nsg_search_batched", [P, P, i64, P, P, i32, i32, P, P, P, P, P], i32),
+    ("nsg_plan_create", [P, P, i64, P, P, i32, i32, P, P, P, P, i32, P, P], i32),
+    ("nsg_plan_run", [P, P], i32),
+    ("nsg_plan_info", [P, P], i32),
+    ("nsg_plan_free", [P], None),
     ("nsg_stop_train", [P, P, P, i64, i32, i32, C.c_float, u64, P, P, P, P], i32),
     ("nsg_index_info", [P, P], i32),
     ("nsg_index_prepare", [P, i32, P], i32),
@@ -291,8 +296,71 @@ class Index:
                                       _ptr(flag), _ptr(steps), cap, _stream()), "nsg_search_trace")
         return dict(ids=ids, feat=feat, flag=flag, steps=steps)
 
+    def search_batched(self, queries, k, L, kmax=None, Lmax=None, params=None):
+        """Uneven batch: per-query k (int32 [nq]) and L (int32 [nq]) in one
+        persistent launch.  Returns ids [nq][kmax], d2, status."""
+        queries = _dev(queries, torch.float32)
+        k, L = _dev(k, torch.int32), _dev(L, torch.int32)
+        nq = queries.shape[0]
+        kmax = int(k.max().item()) if kmax is None else kmax
+        Lmax = int(L.max().item()) if Lmax is None else Lmax
+        dev = queries.device
+        ids = torch.empty((nq, kmax), dtype=torch.int32, device=dev)
+        d2 = torch.empty((nq, kmax), dtype=torch.float32, device=dev)
+        st = torch.empty(nq, dtype=torch.int32, device=dev)
+        p = params if params is not None else SearchParams()
+        _check(lib().nsg_search_batched(self.h, _ptr(queries), nq, _ptr(k), _ptr(L), kmax, Lmax, C.byref(p),
+                                        _ptr(ids), _ptr(d2), _ptr(st), _stream()), "nsg_search_batched")
+        return dict(ids=ids, d2=d2, status=st)
+
+    def plan(self, queries, k, L, kmax=None, Lmax=None, params=None, autotune=True):
+        return Plan(self, queries, k, L, kmax, Lmax, params, autotune)
+
     def save(self, path):
         _check(lib().nsg_save(self.h, path.encode()), "nsg_save")
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("warps_per_cta", C.c_int32), ("hash_slots", C.c_int32), ("n_tried", C.c_int32),
+                ("best_ms", C.c_float), ("worst_ms", C.c_float)]
+
+
+class Plan:
+    """A bound, autotuned, graph-captured batched search (nsg_plan_*).  The
+    tensors passed in stay bound: change their contents, then run()."""
+
+    def __init__(self, index, queries, k, L, kmax, Lmax, params, autotune):
+        self.index = index  # keep the index alive
+        self.queries = _dev(queries, torch.float32)
+        self.k, self.L = _dev(k, torch.int32), _dev(L, torch.int32)
+        nq = self.queries.shape[0]
+        self.kmax = int(self.k.max().item()) if kmax is None else kmax
+        Lmax = int(self.L.max().item()) if Lmax is None else Lmax
+        dev = self.queries.device
+        self.ids = torch.empty((nq, self.kmax), dtype=torch.int32, device=dev)
+        self.d2 = torch.empty((nq, self.kmax), dtype=torch.float32, device=dev)
+        self.status = torch.empty(nq, dtype=torch.int32, device=dev)
+        self.params = params if params is not None else SearchParams()
+        self.h = C.c_void_p()
+        _check(lib().nsg_plan_create(index.h, _ptr(self.queries), nq, _ptr(self.k), _ptr(self.L), self.kmax, Lmax,
+                                     C.byref(self.params), _ptr(self.ids), _ptr(self.d2), _ptr(self.status),
+                                     1 if autotune else 0, _stream(), C.byref(self.h)), "nsg_plan_create")
+
+    def run(self):
+        _check(lib().nsg_plan_run(self.h, _stream()), "nsg_plan_run")
+        return self.ids, self.d2
+
+    def info(self):
+        inf = PlanInfo()
+        _check(lib().nsg_plan_info(self.h, C.byref(inf)), "nsg_plan_info")
+        return {f: getattr(inf, f) for f, _ in inf._fields_}
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().nsg_plan_free(self.h)
+        except Exception:
+            pass
 
 
 def nsg_build(base, K, L, R, Cap, seed=0):

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -669,6 +670,177 @@ nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t
     NSG_CK(nsg::launch_search(l, S(stream)));
     return NSG_OK;
 }
+
+}  // extern "C"
+
+struct nsg_plan {
+    nsg::SearchLaunch l;
+    int *order = nullptr;  // visiting order (longest pool first)
+    int *work = nullptr;   // device work counter
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    nsg_plan_info_t info = {0, 0, 0, 0.0f, 0.0f};
+};
+
+namespace {
+
+void plan_destroy(nsg_plan *p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->order) cudaFree(p->order);
+    if (p->work) cudaFree(p->work);
+    delete p;
+}
+
+// Validated batched launch with its visiting order (queries sorted by pool
+// size, largest first, so the longest searches start first) and work counter.
+nsg_status batched_setup(const nsg_index *idx, const float *queries_dev, int64_t nq, const int32_t *k_dev,
+                         const int32_t *L_dev, int32_t kmax, int32_t Lmax, const nsg_search_params *params,
+                         int32_t *ids_dev, float *d2_dev, int32_t *status_dev, nsg::SearchLaunch &l,
+                         DevBuf<int> &order, DevBuf<int> &work, cudaStream_t st) {
+    if (!k_dev || !L_dev || kmax < 1 || Lmax < kmax) return NSG_EINVAL;
+    nsg_status s = make_search(idx, queries_dev, nq, kmax, Lmax, params, ids_dev, d2_dev, nullptr, nullptr,
+                               status_dev, l);
+    if (s) return s;
+    std::vector<int> hL((size_t)nq), ord((size_t)nq);
+    NSG_CK(cudaMemcpyAsync(hL.data(), L_dev, sizeof(int) * nq, cudaMemcpyDeviceToHost, st));
+    NSG_CK(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < nq; ++i) ord[i] = (int)i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return hL[a] > hL[b]; });
+    NSG_CK(order.alloc((size_t)nq));
+    NSG_CK(work.alloc(1));
+    NSG_CK(cudaMemcpyAsync(order.p, ord.data(), sizeof(int) * nq, cudaMemcpyHostToDevice, st));
+    NSG_CK(cudaStreamSynchronize(st));
+    l.kv = k_dev;
+    l.Lv = L_dev;
+    l.order = order.p;
+    l.work = work.p;
+    return NSG_OK;
+}
+
+nsg_status batched_run(const nsg::SearchLaunch &l, cudaStream_t st) {
+    NSG_CK(cudaMemsetAsync(l.work, 0, sizeof(int), st));
+    NSG_CK(nsg::launch_search(l, st));
+    return NSG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nsg_status nsg_search_batched(const nsg_index *idx, const float *queries_dev, int64_t nq, const int32_t *k_dev,
+                              const int32_t *L_dev, int32_t kmax, int32_t Lmax, const nsg_search_params *params,
+                              int32_t *ids_dev, float *d2_dev, int32_t *status_dev, void *stream) {
+    if (nq == 0 && idx) return NSG_OK;
+    cudaStream_t st = S(stream);
+    nsg::SearchLaunch l;
+    DevBuf<int> order, work;
+    nsg_status s = batched_setup(idx, queries_dev, nq, k_dev, L_dev, kmax, Lmax, params, ids_dev, d2_dev,
+                                 status_dev, l, order, work, st);
+    if (s) return s;
+    s = batched_run(l, st);
+    if (s) return s;
+    NSG_CK(cudaStreamSynchronize(st));  // the order / counter scratch is freed on return
+    return NSG_OK;
+}
+
+nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64_t nq, const int32_t *k_dev,
+                           const int32_t *L_dev, int32_t kmax, int32_t Lmax, const nsg_search_params *params,
+                           int32_t *ids_dev, float *d2_dev, int32_t *status_dev, int32_t autotune, void *stream,
+                           nsg_plan **out) {
+    if (!out) return NSG_EINVAL;
+    *out = nullptr;
+    if (nq < 1) return NSG_EINVAL;
+    cudaStream_t st = S(stream);
+    nsg_plan *p = new (std::nothrow) nsg_plan;
+    if (!p) return NSG_ENOMEM;
+    DevBuf<int> order, work;
+    nsg_status s = batched_setup(idx, queries_dev, nq, k_dev, L_dev, kmax, Lmax, params, ids_dev, d2_dev,
+                                 status_dev, p->l, order, work, st);
+    if (s) {
+        plan_destroy(p);
+        return s;
+    }
+    p->order = order.release();
+    p->work = work.release();
+    if (autotune) {  // time each launch shape on the bound batch; keep the fastest
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f, worst = 0.0f;
+        int bw = 0, bh = 0, tried = 0;
+        for (int w : {2, 4, 8})
+            for (int h : {512, 1024, 2048}) {
+                nsg::SearchLaunch t = p->l;
+                t.warps_per_cta = w;
+                t.hash_slots = h;
+                if (batched_run(t, st) || cudaStreamSynchronize(st) != cudaSuccess) continue;
+                cudaEventRecord(e0, st);
+                bool ok = true;
+                for (int r = 0; r < 3 && ok; ++r) ok = batched_run(t, st) == NSG_OK;
+                cudaEventRecord(e1, st);
+                if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= 3.0f;
+                ++tried;
+                worst = ms > worst ? ms : worst;
+                if (ms < best) {
+                    best = ms;
+                    bw = w;
+                    bh = h;
+                }
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (tried) {
+            p->l.warps_per_cta = bw;
+            p->l.hash_slots = bh;
+            p->info.best_ms = best;
+            p->info.worst_ms = worst;
+        }
+        p->info.n_tried = tried;
+    }
+    p->info.warps_per_cta = p->l.warps_per_cta > 0 ? p->l.warps_per_cta : 4;
+    p->info.hash_slots = p->l.hash_slots;
+    // capture "reset counter + search" once; a run replays it
+    s = batched_run(p->l, st);  // sets kernel attributes outside the capture
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (!s && e != cudaSuccess) s = cuda_fail(e, "plan warm-up");
+    cudaStream_t cs = nullptr;
+    if (!s && (e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) s = cuda_fail(e, "stream");
+    if (!s && (e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+        s = cuda_fail(e, "begin capture");
+    if (!s) {
+        nsg_status r = batched_run(p->l, cs);
+        e = cudaStreamEndCapture(cs, &p->graph);
+        if (r) s = r;
+        else if (e != cudaSuccess) s = cuda_fail(e, "end capture");
+    }
+    if (!s && (e = cudaGraphInstantiate(&p->exec, p->graph, 0)) != cudaSuccess) s = cuda_fail(e, "instantiate");
+    if (cs) cudaStreamDestroy(cs);
+    if (s) {
+        plan_destroy(p);
+        return s;
+    }
+    *out = p;
+    return NSG_OK;
+}
+
+nsg_status nsg_plan_run(nsg_plan *plan, void *stream) {
+    if (!plan || !plan->exec) return NSG_EINVAL;
+    NSG_CK(cudaGraphLaunch(plan->exec, S(stream)));
+    return NSG_OK;
+}
+
+nsg_status nsg_plan_info(const nsg_plan *plan, nsg_plan_info_t *info) {
+    if (!plan || !info) return NSG_EINVAL;
+    *info = plan->info;
+    return NSG_OK;
+}
+
+void nsg_plan_free(nsg_plan *plan) { plan_destroy(plan); }
 
 nsg_status nsg_search_trace(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k, int32_t L,
                             const nsg_search_params *params, int32_t *ids_dev, float *feat_dev,

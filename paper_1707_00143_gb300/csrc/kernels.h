@@ -38,6 +38,10 @@ struct SearchLaunch {
     float *trace_feat = nullptr;           // [nq][trace_cap][8]
     unsigned char *trace_flag = nullptr;   // [nq][trace_cap]
     int trace_cap = 0;
+    // batched uneven queries: per-query k / L (k, L are then the maxima),
+    // visiting order, device work counter (reset before each launch)
+    const int *kv = nullptr, *Lv = nullptr, *order = nullptr;
+    int *work = nullptr;
 };
 cudaError_t launch_search(const SearchLaunch &a, cudaStream_t st);
 
@@ -139,6 +143,10 @@ cudaError_t launch_knn_direct(const KnnLaunch &a, cudaStream_t st);
 // answer (integer values 0..255, d <= 128, k <= 256): *used = 1 when it ran,
 // 0 when it does not apply (nothing written).  Synchronises the stream.
 cudaError_t launch_knn_tc(const KnnLaunch &a, int *used, cudaStream_t st);
+
+// Exact FP32 re-rank: for query i, the k smallest (d2, id) among the KL
+// candidate ids cand[i][..] (-1 = none) into a.ids / a.d2.
+cudaError_t launch_knn_rerank(const KnnLaunch &a, const int *cand, int KL, cudaStream_t st);
 
 // Padding copy [n][d] -> [n][dp] (zeros in the pad).
 cudaError_t launch_pad_rows(const float *src, int64_t n, int d, float *dst, int dp, cudaStream_t st);

@@ -10,6 +10,7 @@
 // into its sorted top-k list in shared memory (warp_merge).
 #include "common.cuh"
 #include "kernels.h"
+#include "search_core.cuh"
 
 namespace nsg {
 
@@ -171,6 +172,89 @@ cudaError_t launch_knn_direct(const KnnLaunch &l, cudaStream_t st) {
     int64_t grid = (l.nq + KD_QPB - 1) / KD_QPB;
     knn_direct_kernel<<<(unsigned)grid, KD_WARPS * 32, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+}  // namespace nsg
+
+// ---------------------------------------------------------------------------
+// Exact re-rank of tensor-core candidates (float data): warp per query; the
+// candidates' FP32 distances come from the same row-distance routine as the
+// search, and the k smallest keys are kept with warp_merge.
+// ---------------------------------------------------------------------------
+namespace nsg {
+
+struct RerankArgs {
+    const float4 *base4;
+    int dp4;
+    const float *queries;  // [nq][dp] (self join: base rows q0..)
+    int64_t nq;
+    const int *cand;
+    int KL, k;
+    int *ids;
+    float *d2;
+};
+
+template <int G, int V, int U>
+__global__ void __launch_bounds__(256) knn_rerank_kernel(RerankArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const unsigned lane = lane_id();
+    const size_t per = 8ull * (32 + a.k + 64) + 4ull * (32 + 64);
+    unsigned char *base = smem + warp * ((per + 15) & ~size_t(15));
+    uint64_t *keys = reinterpret_cast<uint64_t *>(base);
+    uint64_t *list = keys + 32;
+    uint64_t *ck = list + a.k, *sk = ck + 32;
+    int *ids = reinterpret_cast<int *>(sk + 32);
+    int *cp = ids + 32, *sp = cp + 32;
+    for (int64_t q = (int64_t)blockIdx.x * wpb + warp; q < a.nq; q += (int64_t)gridDim.x * wpb) {
+        RowQuery<G, V> Q;
+        Q.load_row(reinterpret_cast<const float4 *>(a.queries) + q * a.dp4, a.dp4);
+        int size = 0;
+        for (int c0 = 0; c0 < a.KL; c0 += 32) {
+            const int c = c0 + (int)lane;
+            const int id = c < a.KL ? a.cand[q * a.KL + c] : -1;
+            const unsigned bal = __ballot_sync(NSG_FULL, id >= 0);
+            if (id >= 0) ids[__popc(bal & lanemask_lt())] = id;
+            const int m = __popc(bal);
+            __syncwarp();
+            if (m == 0) break;
+            rows_dist<G, V, U>(Q, a.base4, a.dp4, ids, m, keys);
+            warp_merge(list, a.k, size, keys, m, ck, cp, sk, sp);
+        }
+        for (int t = lane; t < a.k; t += 32) {
+            a.ids[q * a.k + t] = t < size ? kid(list[t]) : -1;
+            if (a.d2) a.d2[q * a.k + t] = t < size ? kd2(list[t]) : __int_as_float(0x7f800000);
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_knn_rerank(const KnnLaunch &l, const int *cand, int KL, cudaStream_t st) {
+    RerankArgs a;
+    a.base4 = reinterpret_cast<const float4 *>(l.base);
+    a.dp4 = l.dp / 4;
+    a.queries = l.self_join ? l.base + l.q0 * l.dp : l.queries;
+    a.nq = l.nq;
+    a.cand = cand;
+    a.KL = KL;
+    a.k = l.k;
+    a.ids = l.ids;
+    a.d2 = l.d2;
+    const int wpb = 8;
+    const size_t per = ((8ull * (32 + l.k + 64) + 4ull * (32 + 64)) + 15) & ~size_t(15);
+    const size_t smem = per * wpb;
+    const int64_t blocks = (l.nq + wpb - 1) / wpb;
+    const int grid = (int)(blocks < (int64_t)sm_count() * 16 ? blocks : (int64_t)sm_count() * 16);
+    cudaError_t e = cudaSuccess;
+    NSG_DISPATCH_DP4(a.dp4, {
+        auto kern = knn_rerank_kernel<G_, V_, U_>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) {
+            kern<<<grid, wpb * 32, smem, st>>>(a);
+            e = cudaGetLastError();
+        }
+    });
+    return e;
 }
 
 }  // namespace nsg

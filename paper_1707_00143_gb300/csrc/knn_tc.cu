@@ -44,17 +44,22 @@ struct TcArgs {
     const float *xn;  // [ntiles * 128] squared norms of the base rows
     int64_t m, n, q0;
     int self_join, KL, ntiles;
+    int kb;  // 64-wide K chunks per row (streaming form)
     int *ids;
     float *d2;
     int *err;
 };
 
+// DK = 64 or 128: the 128-row query tile stays in shared memory and a stage
+// holds one base tile.  DK = 0: rows wider than 128 values; a stage holds one
+// 64-wide K chunk of both the query tile and the base tile (16 KB each), and
+// a tile takes dk/64 stages.
 template <int DK>
 struct TcCfg {
-    static constexpr int KB = DK / TC_BOXK;                     // swizzle atoms along K
+    static constexpr int KB = DK / TC_BOXK;                     // swizzle atoms along K (resident form)
     static constexpr int A_BYTES = TC_M * DK * 2;
-    static constexpr int B_BYTES = TC_N * DK * 2;               // one pipeline stage
-    static constexpr int NS = DK == 64 ? 8 : 4;                 // stages
+    static constexpr int B_BYTES = DK ? TC_N * DK * 2 : 2 * TC_N * 128;  // one pipeline stage
+    static constexpr int NS = DK == 64 ? 8 : (DK == 128 ? 4 : 5);       // stages
     static constexpr int OFF_B = A_BYTES;
     static constexpr int OFF_BUF = OFF_B + NS * B_BYTES;
     static constexpr int OFF_WARP = OFF_BUF + TC_M * TC_BUF * 8;
@@ -187,26 +192,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            tc::mbar_expect_tx(a_full, Cfg::A_BYTES);
-            for (int kb = 0; kb < Cfg::KB; ++kb)
-                tc::tma_load_2d(sA + kb * (TC_M * 128), &tmA, a_full, kb * TC_BOXK, (int)row0);
+            if (DK) {
+                tc::mbar_expect_tx(a_full, Cfg::A_BYTES);
+                for (int kb = 0; kb < Cfg::KB; ++kb)
+                    tc::tma_load_2d(sA + kb * (TC_M * 128), &tmA, a_full, kb * TC_BOXK, (int)row0);
+            }
+            const int per_tile = DK ? 1 : a.kb;  // stages per tile
             int issued = 0;
-            for (int t = 0; t < a.ntiles; ++t) {
-                const int s = t % Cfg::NS;
-                if (!tc::mbar_wait(b_empty + s, ((t / Cfg::NS) & 1) ^ 1, abort, gerr)) break;
+            for (int c = 0; c < a.ntiles * per_tile; ++c) {
+                const int s = c % Cfg::NS, t = c / per_tile, kc = c - t * per_tile;
+                if (!tc::mbar_wait(b_empty + s, ((c / Cfg::NS) & 1) ^ 1, abort, gerr)) break;
                 tc::mbar_expect_tx(b_full + s, Cfg::B_BYTES);
                 unsigned char *dst = sB + s * Cfg::B_BYTES;
-                for (int kb = 0; kb < Cfg::KB; ++kb)
-                    tc::tma_load_2d(dst + kb * (TC_N * 128), &tmB, b_full + s, kb * TC_BOXK, t * TC_N);
-                issued = t + 1;
+                if (DK) {
+                    for (int kb = 0; kb < Cfg::KB; ++kb)
+                        tc::tma_load_2d(dst + kb * (TC_N * 128), &tmB, b_full + s, kb * TC_BOXK, t * TC_N);
+                } else {
+                    tc::tma_load_2d(dst, &tmA, b_full + s, kc * TC_BOXK, (int)row0);
+                    tc::tma_load_2d(dst + TC_M * 128, &tmB, b_full + s, kc * TC_BOXK, t * TC_N);
+                }
+                issued = c + 1;
             }
             if (*abort) {
                 // drain: wait (bounded) for the copies still in flight
                 volatile int local = 0;
-                tc::mbar_wait(a_full, 0, &local, nullptr);
-                for (int t = issued - Cfg::NS < 0 ? 0 : issued - Cfg::NS; t < issued; ++t) {
+                if (DK) tc::mbar_wait(a_full, 0, &local, nullptr);
+                for (int c = issued - Cfg::NS < 0 ? 0 : issued - Cfg::NS; c < issued; ++c) {
                     local = 0;
-                    tc::mbar_wait(b_full + t % Cfg::NS, (t / Cfg::NS) & 1, &local, nullptr);
+                    tc::mbar_wait(b_full + c % Cfg::NS, (c / Cfg::NS) & 1, &local, nullptr);
                 }
             }
         }
@@ -215,21 +228,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16_f32(TC_M, TC_N);
             const uint32_t a_base = tc::smem_u32(sA), b_base = tc::smem_u32(sB);
-            bool ok = tc::mbar_wait(a_full, 0, abort, gerr);
+            bool ok = DK ? tc::mbar_wait(a_full, 0, abort, gerr) : true;
+            const int per_tile = DK ? 1 : a.kb;
+            int c = 0;
             for (int t = 0; ok && t < a.ntiles; ++t) {
-                const int buf = t & 1, s = t % Cfg::NS;
+                const int buf = t & 1;
                 if (!tc::mbar_wait(acc_empty + buf, ((t >> 1) & 1) ^ 1, abort, gerr)) break;
                 tc::fence_after_sync();
-                if (!tc::mbar_wait(b_full + s, (t / Cfg::NS) & 1, abort, gerr)) break;
-                tc::fence_after_sync();
+                for (int kc = 0; ok && kc < per_tile; ++kc, ++c) {
+                    const int s = c % Cfg::NS;
+                    if (!tc::mbar_wait(b_full + s, (c / Cfg::NS) & 1, abort, gerr)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    if (DK) {
 #pragma unroll
-                for (int kk = 0; kk < DK / 16; ++kk) {
-                    const uint32_t koff = (kk >> 2) * (TC_M * 128) + (kk & 3) * 32;
-                    const uint32_t boff = s * Cfg::B_BYTES + (kk >> 2) * (TC_N * 128) + (kk & 3) * 32;
-                    tc::mma_bf16(tmem + buf * TC_N, tc::sdesc_sw128(a_base + koff),
-                                 tc::sdesc_sw128(b_base + boff), idesc, kk > 0 ? 1u : 0u);
+                        for (int kk = 0; kk < (DK ? DK : 64) / 16; ++kk) {
+                            const uint32_t koff = (kk >> 2) * (TC_M * 128) + (kk & 3) * 32;
+                            const uint32_t boff = s * Cfg::B_BYTES + (kk >> 2) * (TC_N * 128) + (kk & 3) * 32;
+                            tc::mma_bf16(tmem + buf * TC_N, tc::sdesc_sw128(a_base + koff),
+                                         tc::sdesc_sw128(b_base + boff), idesc, kk > 0 ? 1u : 0u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t st = b_base + s * Cfg::B_BYTES + kk * 32;
+                            tc::mma_bf16(tmem + buf * TC_N, tc::sdesc_sw128(st), tc::sdesc_sw128(st + TC_M * 128),
+                                         idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                        }
+                    }
+                    tc::mma_commit(b_empty + s);
                 }
-                tc::mma_commit(b_empty + s);
+                if (!ok) break;
                 tc::mma_commit(acc_full + buf);
             }
             // every MMA issued so far has completed before TMEM is released
@@ -285,7 +316,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const float tv = fmaf(-2.0f, __uint_as_float(v[h * 16 + j]), xs[jj]);
                         const int64_t col = col0 + jj;
                         if (valid && tv < thrp && col < a.n && col != self_id) {
-                            mybuf[cnt] = make_key(qn_r + tv, (int)col);
+                            mybuf[cnt] = make_key(fmaxf(qn_r + tv, 0.0f), (int)col);
                             ++cnt;
                         }
                     }
@@ -395,8 +426,8 @@ struct Scratch {
 // d <= 128, k <= 256); *used = 0 when it does not apply (nothing written).
 cudaError_t launch_knn_tc(const KnnLaunch &l, int *used, cudaStream_t st) {
     *used = 0;
-    if (l.nq <= 0 || l.k > TC_MAXK || l.dp > 128 || !encode_fn()) return cudaSuccess;
-    const int dk = l.dp <= 64 ? 64 : 128;
+    if (l.nq <= 0 || l.k > TC_MAXK || l.dp > 1024 || !encode_fn()) return cudaSuccess;
+    const int dk = l.dp <= 64 ? 64 : (l.dp <= 128 ? 128 : (l.dp + 63) / 64 * 64);
     const int64_t ntiles = (l.n + TC_N - 1) / TC_N;
     if (ntiles > INT32_MAX / TC_N) return cudaSuccess;
     const int64_t npad = ntiles * TC_N;
@@ -423,16 +454,29 @@ cudaError_t launch_knn_tc(const KnnLaunch &l, int *used, cudaStream_t st) {
     int h[2] = {0, 0};
     if ((e = cudaMemcpyAsync(h, flag.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-    if (h[0]) return cudaSuccess;  // not integer 0..255: the exact CUDA-core scan is used instead
+    // Integer data 0..255 with d <= 128: the GEMM-form distances are exact and
+    // the k best lists are the answer.  Otherwise (float data, or wider rows
+    // whose integer sums may pass 2^24) the GEMM keeps the KL = k + margin best
+    // candidates by its BF16 distance and an exact FP32 re-rank picks the k.
+    const bool exact = !h[0] && dk <= 128;
+    const int KL = exact ? l.k : (l.k + (l.k / 2 > 32 ? l.k / 2 : 32) < TC_MAXK ? l.k + (l.k / 2 > 32 ? l.k / 2 : 32)
+                                                                                 : TC_MAXK);
+    if (!exact && KL < l.k + 16) return cudaSuccess;  // no room for a margin: exact scan instead
     CUtensorMap mA, mB;
     const int64_t arows = l.self_join ? l.n - l.q0 : l.nq;
     if (!make_map(&mA, qsrc, arows, dk, TC_M) || !make_map(&mB, xb.p, l.n, dk, TC_N)) return cudaSuccess;
-    // the rows' sorted lists live in the output arrays: distances are needed
-    // even when the caller asked for ids only
+    // the rows' sorted lists live in the output arrays (exact) or in scratch
+    // (candidates); distances are kept even when the caller asked for ids only
     Scratch<float> d2s;
+    Scratch<int> ids_s;
     float *d2out = l.d2;
-    if (!d2out) {
-        if ((e = d2s.alloc((size_t)l.nq * l.k)) != cudaSuccess) return e;
+    int *idsout = l.ids;
+    if (!exact) {
+        if ((e = ids_s.alloc((size_t)l.nq * KL)) != cudaSuccess) return e;
+        idsout = ids_s.p;
+    }
+    if (!exact || !d2out) {
+        if ((e = d2s.alloc((size_t)l.nq * KL)) != cudaSuccess) return e;
         d2out = d2s.p;
     }
     TcArgs a;
@@ -442,9 +486,10 @@ cudaError_t launch_knn_tc(const KnnLaunch &l, int *used, cudaStream_t st) {
     a.n = l.n;
     a.q0 = l.q0;
     a.self_join = l.self_join;
-    a.KL = l.k;
+    a.KL = KL;
     a.ntiles = (int)ntiles;
-    a.ids = l.ids;
+    a.kb = dk / TC_BOXK;
+    a.ids = idsout;
     a.d2 = d2out;
     a.err = flag.p + 1;
     const int64_t grid = (l.nq + TC_M - 1) / TC_M;
@@ -454,17 +499,27 @@ cudaError_t launch_knn_tc(const KnnLaunch &l, int *used, cudaStream_t st) {
             cudaSuccess)
             return e;
         kern<<<(unsigned)grid, TC_THREADS, TcCfg<64>::SMEM, st>>>(mA, mB, a);
-    } else {
+    } else if (dk == 128) {
         auto kern = knn_tc_kernel<128>;
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<128>::SMEM)) !=
             cudaSuccess)
             return e;
         kern<<<(unsigned)grid, TC_THREADS, TcCfg<128>::SMEM, st>>>(mA, mB, a);
+    } else {
+        auto kern = knn_tc_kernel<0>;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<0>::SMEM)) !=
+            cudaSuccess)
+            return e;
+        kern<<<(unsigned)grid, TC_THREADS, TcCfg<0>::SMEM, st>>>(mA, mB, a);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(h, flag.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
     if (h[1]) return cudaErrorLaunchTimeout;  // a pipeline wait gave up (bounded waits)
+    if (!exact) {
+        if ((e = launch_knn_rerank(l, idsout, KL, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;  // scratch is freed on return
+    }
     *used = 1;
     return cudaSuccess;
 }

@@ -57,6 +57,11 @@ struct SearchArgs {
     float *trace_feat;
     unsigned char *trace_flag;
     int trace_cap;
+    // batched uneven queries: per-query k and L (k, L above are the maxima and
+    // the output row stride is k), a visiting order and a work counter that
+    // persistent warps draw from (nullptr: static grid-stride assignment)
+    const int *kv, *Lv, *order;
+    int *work;
 };
 
 // Alg. 1 per query.  P = PREC_F32: distances on the FP32 rows (the plain
@@ -79,12 +84,23 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
     }
     int csize = 0;
     const int64_t stride = (int64_t)gridDim.x * wpb;
-    for (int64_t qi = (int64_t)blockIdx.x * wpb + warp; qi < a.nq; qi += stride) {
+    int64_t t = (int64_t)blockIdx.x * wpb + warp;
+    for (;;) {
+        if (a.work != nullptr) {  // persistent warps draw the next query
+            int v = 0;
+            if (lane == 0) v = atomicAdd(a.work, 1);
+            t = __shfl_sync(NSG_FULL, v, 0);
+        }
+        if (t >= a.nq) break;
+        const int64_t qi = a.order != nullptr ? a.order[t] : t;
+        if (a.work == nullptr) t += stride;
+        const int kq = a.kv != nullptr ? min(max(a.kv[qi], 1), a.k) : a.k;
+        const int Lq = a.Lv != nullptr ? max(min(a.Lv[qi], a.L), kq) : a.L;
         const float *qp = a.queries + qi * a.d;
         StopCtx sc;
         sc.mlp = a.stop_model != nullptr ? mlp : nullptr;
         sc.logit = a.stop_logit;
-        sc.k = a.stop_k;
+        sc.k = a.kv != nullptr ? min(kq, a.stop_k) : a.stop_k;
         sc.min_steps = a.stop_min_steps;
         sc.trace_feat = a.trace_feat != nullptr ? a.trace_feat + qi * (int64_t)a.trace_cap * NSG_STOP_NF : nullptr;
         sc.trace_flag = a.trace_flag != nullptr ? a.trace_flag + qi * (int64_t)a.trace_cap : nullptr;
@@ -94,7 +110,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
         if constexpr (P == PREC_F32) {
             DistF32<G, V, U> dist{{}, a.base4, a.dp4};
             dist.Q.load(qp, a.d, a.dp4);
-            o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, a.L, s,
+            o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, Lq, s,
                                                               (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
                                                               csize, nullptr, 0, scp);
         } else {
@@ -103,7 +119,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
             constexpr int UL = VC <= 1 ? NSG_UL1 : (VC == 2 ? NSG_UL2 : 2);
             DistLp<P, G, VC, UL> dist{{}, a.lowp, a.dc};
             dist.Q.load(qp, a.d, a.scale);
-            o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, a.L, s,
+            o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, Lq, s,
                                                               (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
                                                               csize, nullptr, 0, scp);
         }
@@ -118,15 +134,16 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
                 for (int t = lane; t < mm; t += 32) s.ids[t] = kid(s.pool[c0 + t]);
                 __syncwarp();
                 exact(s.ids, mm, s.keys);
-                warp_merge(s.clist, a.C, kept, s.keys, mm, s.ck, s.cp, s.sk, s.sp);
+                warp_merge(s.clist, kq, kept, s.keys, mm, s.ck, s.cp, s.sk, s.sp);
             }
             res = s.clist;
             rsize = kept;
         }
-        for (int t = lane; t < a.k; t += 32) {
-            uint64_t e = t < rsize ? res[t] : KEY_INF;
-            a.ids[qi * a.k + t] = t < rsize ? kid(e) : -1;
-            if (a.d2) a.d2[qi * a.k + t] = t < rsize ? kd2(e) : __int_as_float(0x7f800000);
+        for (int c = lane; c < a.k; c += 32) {  // row stride a.k; slots past this query's k padded
+            const bool has = c < rsize && c < kq;
+            uint64_t e = has ? res[c] : KEY_INF;
+            a.ids[qi * a.k + c] = has ? kid(e) : -1;
+            if (a.d2) a.d2[qi * a.k + c] = has ? kd2(e) : __int_as_float(0x7f800000);
         }
         if (lane == 0) {
             if (a.n_expand) a.n_expand[qi] = o.n_expand;
@@ -262,6 +279,10 @@ cudaError_t launch_search(const SearchLaunch &l, cudaStream_t st) {
     a.trace_feat = l.trace_feat;
     a.trace_flag = l.trace_flag;
     a.trace_cap = l.trace_cap;
+    a.kv = l.kv;
+    a.Lv = l.Lv;
+    a.order = l.order;
+    a.work = l.work;
     size_t per_warp = warp_smem_bytes(a.L, a.W, a.C, a.H);
     const size_t per_cta = l.stop_model ? ((sizeof(StopMLP) + 15) & ~size_t(15)) : 0;
     cudaError_t err = cudaSuccess;

@@ -2,9 +2,11 @@
 
 Integer data in 0..255 with d <= 128 takes the tensor-core path (BF16 GEMM,
 FP32 accumulation, fused top-k): distances are exact integers there, so ids
-and distances must equal the oracle bit for bit.  Other data takes the exact
-FP32 CUDA-core scan; its distances differ from the oracle's only by summation
-order (relative 1e-5, the tolerance stated for float data)."""
+and distances must equal the oracle bit for bit.  Float data and rows wider
+than 128 keep k + margin candidates by the GEMM distance and re-rank them
+with exact FP32 distances; those differ from the oracle's only by summation
+order (relative 1e-5, the tolerance stated for float data).  Rows wider than
+1024 take the exact FP32 CUDA-core scan."""
 import os
 
 import numpy as np
@@ -74,8 +76,9 @@ def test_float_data_uses_exact_scan_within_tolerance(nsg):
     assert np.allclose(d2, exact, rtol=1e-5, atol=0)
 
 
-def test_knn_large_d_uses_scan_bit_exact(nsg):
-    # d = 200 > 128: the CUDA-core scan; integer data is still exact in any order
+def test_knn_large_d_bit_exact(nsg):
+    # d = 200 > 128: the streaming tensor-core form (64-wide K chunks) keeps
+    # candidates, the FP32 re-rank picks the k; integer data is exact in any order
     base = datagen.uniform_int(900, 200, seed=65)
     ids, d2 = nsg.nsg_knn_init(T(base), 30)
     rid, rd2 = oracle.knn_rows(base, 30)
@@ -89,3 +92,31 @@ def test_knn_init_ids_only(nsg):
     assert d2 is None
     rid, _ = oracle.knn_rows(base, 20)
     assert np.array_equal(H(ids), rid)
+
+
+@pytest.mark.parametrize("n,d,k", [(2000, 960, 100), (1500, 1024, 10), (900, 1028, 20)])
+def test_knn_wide_float_rows(nsg, n, d, k):
+    base = datagen.uniform_float(n, d, seed=d)
+    ids, d2 = nsg.nsg_knn_init(T(base), k)
+    rid, rd2 = oracle.knn_rows(base, k)
+    ids, d2 = H(ids), H(d2)
+    assert np.allclose(d2, rd2, rtol=1e-5, atol=0)
+    exact = ((base[ids].astype(np.float64) - base[:, None, :]) ** 2).sum(-1)
+    assert np.allclose(d2, exact, rtol=1e-5, atol=0)
+    assert (ids == rid).mean() > 0.999
+
+
+def test_knn_query_gist_shaped(nsg):
+    base, q = datagen.workload("gist", n=4000, nq=64)
+    ids, d2 = nsg.nsg_knn_query(T(base), T(q), 100)
+    rid, rd2 = oracle.knn_query(base, q, 100)
+    assert np.allclose(H(d2), rd2, rtol=1e-5, atol=0)
+    assert oracle.recall(H(ids), rid, 100) >= 0.999
+
+
+def test_knn_deep_shaped_unit_norm(nsg):
+    base, _ = datagen.workload("deep", n=5000, nq=1)
+    ids, d2 = nsg.nsg_knn_init(T(base), 64)
+    rid, rd2 = oracle.knn_rows(base, 64)
+    assert np.allclose(H(d2), rd2, rtol=1e-5, atol=1e-7)
+    assert oracle.recall(H(ids), rid, 64) >= 0.999
