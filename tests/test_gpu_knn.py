@@ -103,7 +103,10 @@ def test_knn_wide_float_rows(nsg, n, d, k):
     assert np.allclose(d2, rd2, rtol=1e-5, atol=0)
     exact = ((base[ids].astype(np.float64) - base[:, None, :]) ** 2).sum(-1)
     assert np.allclose(d2, exact, rtol=1e-5, atol=0)
-    assert (ids == rid).mean() > 0.999
+    # ids may swap only among near-ties: none is farther than the true k-th
+    # distance beyond rounding, and the sets agree
+    assert (exact <= rd2[:, -1:].astype(np.float64) * (1 + 1e-5)).all()
+    assert oracle.recall(ids, rid, k) >= 0.995
 
 
 def test_knn_query_gist_shaped(nsg):
