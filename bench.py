@@ -8,10 +8,12 @@ paper's Alg. 2 at K=100, L=40, R=50, C=500.  The pool size L is swept over
 mean recall@10 (Eq. 1, against the exact ground truth) is >= 0.95.
 
 Forms: plain (FP32 traversal, exactly Alg. 1), the precision forms (BF16 or
-FP8-e4m3 traversal distances with FP32 accumulation, FP32 re-rank of the
-final pool when the copy is lossy), and the learned-stop forms (an MLP
-trained on the GPU from search traces of a separate query batch ends each
-search early; swept over its probability threshold).  `value` is the form with the highest QPS
+FP8-e4m3 traversal distances with FP32 accumulation, or an 8-bit copy with
+exact int32 sums; FP32 re-rank of the final pool when the copy is lossy),
+and the learned-stop forms (an MLP trained on the GPU from search traces of
+a separate query batch ends each search early; swept over its probability
+threshold).  On this integer workload the BF16 and U8 copies are exact, so
+those forms return the plain form's results bit for bit.  `value` is the form with the highest QPS
 at recall@10 >= 0.95 ("chosen"); `plain` holds the plain form beside it.
 
 A step = one nsg_search_ex launch over the whole 10,000-query batch, inputs
@@ -42,10 +44,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "queries/sec at recall@10=0.95 on 1 GB300, chosen vs plain form; % HBM peak"
 UNIT = "queries/s"
-BUILD = dict(K=100, L=40, R=50, C=500)
-L_GRID = list(range(100, 401, 25))
-K_RESULTS = 100
 TARGET = 0.95
+# Per workload: build parameters, the L grid, result size k, and a description.
+# `sift` is the headline configuration; `gist` (float, d=960) and `deep`
+# (10M x 96 unit vectors) are the precision and batched configurations.
+WORKLOADS = {
+    "sift": dict(build=dict(K=100, L=40, R=50, C=500), L_grid=list(range(100, 401, 25)), k=100,
+                 desc="sift-shaped 1,000,000 x 128 int 0..255 GMM(100), 10,000 queries"),
+    "gist": dict(build=dict(K=100, L=60, R=70, C=500), L_grid=[10, 20, 40, 60, 80, 100, 150, 200, 300, 400, 500],
+                 k=100, desc="gist-shaped 1,000,000 x 960 f32 [0,1] GMM(50), 1,000 queries"),
+    "deep": dict(build=dict(K=64, L=60, R=32, C=500), L_grid=[20, 40, 60, 80, 100, 150, 200, 300, 400, 500],
+                 k=100, desc="deep-shaped 10,000,000 x 96 f32 unit-norm GMM(1000), 100,000 queries"),
+}
 STOP_TRACE_L, STOP_TRACE_CAP, STOP_ITERS = 250, 1024, 300
 STOP_THRESHOLDS = [0.5, 0.7, 0.9]
 FALLBACK_HBM_GBS = 6800.0
@@ -57,7 +67,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="sift")
+    p.add_argument("--workload", default="sift", choices=sorted(WORKLOADS))
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     return p.parse_args()
 
@@ -177,7 +187,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: 1,000,000 x 128 int 0..255, serial scan", "k": 10},
+        "config": {"workload": WORKLOADS[args.workload]["desc"] + ", serial scan", "k": 10},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -208,6 +218,8 @@ def main():
     capi.lib()
 
     # inputs: same base on every rank (a replica), a distinct query batch per rank
+    W = WORKLOADS[args.workload]
+    BUILD, L_GRID, K_RESULTS = W["build"], W["L_grid"], W["k"]
     base, q = datagen.workload(args.workload, seed_query=datagen.SEED_QUERY + 1000 * rank)
     n, d = base.shape
     nq = len(q)
@@ -218,12 +230,12 @@ def main():
     t0 = time.perf_counter()
     idx = capi.nsg_build(bt, BUILD["K"], BUILD["L"], BUILD["R"], BUILD["C"], seed=0)
     build_s = time.perf_counter() - t0
-    gt, _ = capi.nsg_knn_query(bt, qt, 10)
+    gt, gt_d2 = capi.nsg_knn_query(bt, qt, 10)
 
     # the forms: plain FP32 traversal, and the precision forms (BF16 / FP8-e4m3
     # traversal with FP32 accumulation; FP32 re-rank of the pool when the copy is lossy)
     forms = {"plain": capi.SearchParams(0, 0, capi.PREC_F32, 0)}
-    for name, prec in (("bf16", capi.PREC_BF16), ("fp8", capi.PREC_FP8)):
+    for name, prec in (("bf16", capi.PREC_BF16), ("fp8", capi.PREC_FP8), ("u8", capi.PREC_U8)):
         idx.prepare(prec)
         forms[name] = capi.SearchParams(0, 0, prec, 0, -1)
     # learned early termination: traces of a separate query batch (its own
@@ -231,12 +243,12 @@ def main():
     _, q_train = datagen.workload(args.workload, nq=nq, seed_query=datagen.SEED_QUERY + 500 + 1000 * rank)
     t1 = time.perf_counter()
     trace = idx.search_trace(torch.from_numpy(q_train).cuda(), 10, STOP_TRACE_L, STOP_TRACE_CAP,
-                             params=capi.SearchParams(0, 0, capi.PREC_BF16, 0, -1, None, 0.5, 10))
+                             params=capi.SearchParams(0, 0, capi.PREC_F32, 0, -1, None, 0.5, 10))
     stop_model, _, stop_loss = capi.nsg_stop_train(trace, iters=STOP_ITERS, lr=1e-2, seed=1)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
     for th in STOP_THRESHOLDS:
-        for base_name in ("plain", "bf16"):
+        for base_name in ("plain", "u8"):
             b = forms[base_name]
             forms[f"{base_name}+stop{th}"] = capi.SearchParams(0, 0, b.precision, 0, -1, stop_model, th, 10)
     info = idx.info()
@@ -273,6 +285,21 @@ def main():
     L = cands[chosen_form]["L"] if cands else L_GRID[-1]
     prm = forms[chosen_form]
 
+    # traversal-distance error of the precision forms against FP64: search a
+    # query sample without re-rank, recompute the returned ids' distances in
+    # float64 on the host, compare in the copy's units scaled back
+    prec_err = {}
+    qs_n = min(200, nq)
+    for name, scale in (("bf16", 1.0), ("fp8", info["fp8_scale"]), ("u8", info["u8_scale"])):
+        o = idx.search_ex(qt[:qs_n], 10, L_GRID[len(L_GRID) // 2],
+                          params=capi.SearchParams(0, 0, forms[name].precision, 0, 0), counters=False)
+        ids_s = o["ids"].cpu().numpy()
+        d2_s = o["d2"].cpu().numpy().astype(np.float64) / (scale * scale)
+        ex = ((base[ids_s].astype(np.float64) - q[:qs_n, None, :].astype(np.float64)) ** 2).sum(-1)
+        rel = np.abs(d2_s - ex) / np.maximum(ex, 1e-30)
+        prec_err[name] = {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()),
+                          "queries": qs_n, "k": 10, "exact_copy": bool(info["has_" + name] == 2)}
+
     # algorithmic bytes at the chosen point: unique distance and expansion counts
     big = capi.SearchParams(0, 16384, prm.precision, 0, prm.rerank)
     cnt = idx.search_ex(qt, K_RESULTS, L, params=big)
@@ -280,8 +307,10 @@ def main():
     n_expand = cnt["n_expand"].to(torch.int64).sum().item()
     R = info["R"]
     base_form = chosen_form.split("+")[0]
-    row_bytes = {"plain": d * 4, "bf16": ((d + 7) // 8) * 16, "fp8": ((d + 15) // 16) * 16}[base_form]
-    lossy = {"plain": False, "bf16": info["has_bf16"] == 1, "fp8": info["has_fp8"] == 1}[base_form]
+    row_bytes = {"plain": d * 4, "bf16": ((d + 7) // 8) * 16, "fp8": ((d + 15) // 16) * 16,
+                 "u8": ((d + 15) // 16) * 16}[base_form]
+    lossy = {"plain": False, "bf16": info["has_bf16"] == 1, "fp8": info["has_fp8"] == 1,
+             "u8": info["has_u8"] == 1}[base_form]
     bytes_launch = (n_dist * row_bytes + n_expand * R * 4 + nq * (d * 4 + K_RESULTS * 8)
                     + (nq * L * d * 4 if lossy else 0))
 
@@ -298,6 +327,9 @@ def main():
     torch.cuda.synchronize()
     clocks = clk.stop()
     rec_chosen = recall10(out)
+    # tie-aware recall@10: a returned id counts when its distance is within the
+    # true 10th distance (integer data has many exact ties)
+    rec_chosen_ties = (out["d2"][:, :10] <= gt_d2[:, 9:10]).sum().item() / (10.0 * nq)
     ms_plain = timed(forms["plain"], plain_L, args.steps)
     rec_plain = recall10(out)
     if world > 1:
@@ -324,6 +356,28 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = t.item()
 
+    # batched uneven queries on the same index: k from {1, 10, 100}, L uniform
+    # in 20..500, one autotuned persistent launch replayed as a CUDA graph,
+    # against the same batch padded to one fixed (k, L) = (100, 500) launch
+    kb, Lb = datagen.uneven_k_L(nq, seed=91 + rank, ks=(1, 10, 100), l_lo=20, l_hi=500)
+    kbt, Lbt = torch.from_numpy(kb).cuda(), torch.from_numpy(Lb).cuda()
+    bprm = forms[chosen_form.split("+")[0]]
+    plan = idx.plan(qt, kbt, Lbt, params=bprm, autotune=True)
+    pinfo = plan.info()
+    for _ in range(args.warmup):
+        plan.run()
+    ev0.record(st)
+    for _ in range(args.steps):
+        plan.run()
+    ev1.record(st)
+    ev1.synchronize()
+    ms_batched = ev0.elapsed_time(ev1) / args.steps
+    ms_padded = timed(bprm, int(Lb.max()), max(2, args.steps // 2))
+    batched = {"form": chosen_form.split("+")[0], "queries": nq, "k_choices": [1, 10, 100], "L_range": [20, 500],
+               "value": world * nq / (ms_batched / 1e3), "ms_per_step": ms_batched,
+               "padded_k100_L500": {"value": world * nq / (ms_padded / 1e3), "ms_per_step": ms_padded},
+               "plan": pinfo}
+
     peak, peak_kind = peaks()
     achieved = bytes_launch / (ms_step / 1e3) / 1e9
     src = kernel_source_hash()
@@ -342,12 +396,13 @@ def main():
             "metric": METRIC, "value": world * nq / (ms_step / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"plain": "f32", "bf16": "bf16->f32", "fp8": "fp8e4m3->f32"}[base_form],
+            "dtype": {"plain": "f32", "bf16": "bf16->f32", "fp8": "fp8e4m3->f32", "u8": "u8->i32"}[base_form],
             "data": "synthetic",
-            "config": {"workload": "sift-shaped 1,000,000 x 128 int 0..255 GMM(100), 10,000 queries",
+            "config": {"workload": W["desc"],
                        "form": chosen_form, "build": BUILD, "k": K_RESULTS, "L": L,
-                       "recall10": rec_chosen, "target_recall10": TARGET, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (512 MB base)"},
+                       "recall10": rec_chosen, "recall10_ties": rec_chosen_ties, "target_recall10": TARGET,
+                       "parallelism": f"replicas{world}",
+                       "l2": f"inputs larger than L2 ({base.nbytes >> 20} MB base)"},
             "plain": {"value": world * nq / (ms_plain / 1e3), "ms_per_step": ms_plain, "L": plain_L,
                       "recall10": rec_plain},
             "chosen_over_plain": ms_plain / ms_step,
@@ -362,11 +417,14 @@ def main():
                                                "ms_connect", "ms_total")},
             "index": {"avg_degree": info["avg_degree"], "max_degree": info["max_degree"],
                       "fixup_edges": info["n_fixup_edges"], "fixup_researched": info["n_fixup_searches"],
-                      "nav": info["nav"], "bf16_exact": info["has_bf16"] == 2, "fp8_scale": info["fp8_scale"]},
+                      "nav": info["nav"], "bf16_exact": info["has_bf16"] == 2, "u8_exact": info["has_u8"] == 2,
+                      "fp8_scale": info["fp8_scale"]},
             "per_query": {"n_expand": n_expand / nq, "n_dist": n_dist / nq},
+            "batched": batched,
             "learned_stop": {"train_queries": nq, "trace_L": STOP_TRACE_L, "iters": STOP_ITERS,
                              "train_seconds": train_s, "loss_first": stop_loss[0].item(),
                              "loss_last": stop_loss[-1].item(), "thresholds": STOP_THRESHOLDS},
+            "precision_error_vs_fp64": prec_err,
             "sweep": sweeps,
         }
         print(json.dumps(line), flush=True)

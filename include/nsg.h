@@ -47,17 +47,20 @@ typedef enum {
 
 typedef struct nsg_index nsg_index; /* opaque; owns its device memory */
 
-/* Traversal precision of the search (the final pool is always re-ranked in
- * FP32 when a low-precision copy is used). */
-typedef enum { NSG_PREC_F32 = 0, NSG_PREC_BF16 = 1, NSG_PREC_FP8 = 2 } nsg_precision;
+/* Traversal precision of the search.  The final pool is re-ranked on the FP32
+ * rows whenever the copy's distances can differ from the FP32 ones (see
+ * nsg_search_params.rerank).  NSG_PREC_U8 is an 8-bit affine copy with integer
+ * arithmetic (exact on integer data spanning at most 256 values). */
+typedef enum { NSG_PREC_F32 = 0, NSG_PREC_BF16 = 1, NSG_PREC_FP8 = 2, NSG_PREC_U8 = 3 } nsg_precision;
 
 typedef struct {
     int32_t max_steps;     /* expansion cap per query; <= 0 -> 16*L + 4096 */
     int32_t hash_slots;    /* visited-hash slots per query (power of 2, 64..65536); <= 0 -> auto */
     int32_t precision;     /* nsg_precision of the traversal distances */
     int32_t warps_per_cta; /* <= 0 -> auto */
-    int32_t rerank;        /* BF16/FP8: re-rank the final pool with FP32 rows (1), not (0),
-                              or only when the copy is lossy (-1) */
+    int32_t rerank;        /* BF16/FP8/U8: re-rank the final pool with FP32 rows (1), not (0),
+                              or only when the copy is lossy (-1); U8 with -1 also
+                              re-ranks a query whose values the 8-bit map rounds */
     const void *stop_model; /* learned early termination: NSG_STOP_PARAMS FP16 values on the
                                device (see nsg_stop_train), or NULL for the fixed-L search */
     float stop_threshold;  /* stop once the model's probability exceeds this (0..1) */
@@ -85,6 +88,8 @@ typedef struct {
     /* build phase wall times in milliseconds (0 when not built here) */
     float ms_knn, ms_centroid_nav, ms_collect, ms_prune, ms_connect, ms_total;
     int64_t n_fixup_searches; /* fix-ups whose speculative search was stale and ran again */
+    int32_t has_u8;        /* 8-bit copy: 0 none, 1 lossy, 2 every value and distance exact */
+    float u8_lo, u8_scale; /* x_u8 = clamp(rint((x - u8_lo) * u8_scale), 0, 255) */
 } nsg_index_info_t;
 
 /* Human-readable name of a status code (static string). */
@@ -100,6 +105,10 @@ const char *nsg_last_cuda_error(void);
  *   base_dev [n][d] f32; knn_ids_dev [n][K] i32 out; knn_d2_dev [n][K] f32 out
  *   (nullable).  Requires 1 <= K < n, d >= 1.  Uses tensor cores where the
  *   data allows an exact answer, else an exact FP32 scan.  Allocates scratch.
+ *   Environment: NSG_KNN_ENGINE=scan forces the FP32 scan;
+ *   NSG_KNN_CHUNK_TILES=t sets the tensor-core form's base chunk (t tiles of
+ *   128 rows per launch; default ~48 MB of BF16 rows); the chunk size does
+ *   not change results.
  * nsg_knn_query: the k nearest base rows of each query (ground truth):
  *   queries_dev [nq][d]; ids_dev [nq][k]; d2_dev [nq][k] nullable; k <= n.
  * ------------------------------------------------------------------------- */
@@ -213,8 +222,10 @@ nsg_status nsg_index_from_graph(const float *base_dev, int64_t n, int32_t d, con
  *   params->precision BF16 / FP8 (after nsg_index_prepare): traversal
  *   distances on that copy with FP32 accumulation; with re-rank, the L pool
  *   entries are measured again on the FP32 rows and the k smallest returned
- *   (d2 then holds FP32 squared distances; without re-rank, FP8 distances are
- *   in scaled units).
+ *   (d2 then holds FP32 squared distances; without re-rank, FP8 and lossy U8
+ *   distances are in scaled units).  NSG_PREC_U8 sums squared byte
+ *   differences exactly in int32 (__vabsdiffu4 + __dp4a); the query takes the
+ *   copy's 8-bit map.
  * ------------------------------------------------------------------------- */
 nsg_status nsg_search(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k,
                       int32_t L, int32_t *ids_dev, float *d2_dev, void *stream);
@@ -299,7 +310,9 @@ nsg_status nsg_recall(const int32_t *ids_dev, int32_t ld_ids, const int32_t *gt_
 nsg_status nsg_index_info(const nsg_index *idx, nsg_index_info_t *info);
 /* Low-precision copy of the base for the precision forms of nsg_search_ex
  *   (NSG_PREC_BF16: round to nearest; NSG_PREC_FP8: e4m3 of x * s with
- *   s = 448 / max|x|, saturating).  Owned by the index; a no-op when present.
+ *   s = 448 / max|x|, saturating; NSG_PREC_U8: rint((x - lo) * s) with
+ *   lo = min x and s = 1 when every value is an integer and max - min <= 255,
+ *   else s = 255 / (max - min)).  Owned by the index; a no-op when present.
  *   Synchronises the stream. */
 nsg_status nsg_index_prepare(nsg_index *idx, int32_t precision, void *stream);
 nsg_status nsg_index_graph(const nsg_index *idx, int32_t *adj_dev, int32_t *deg_dev, void *stream);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libnsg.so")
 
 NSG_OK, NSG_EINVAL, NSG_ENOMEM, NSG_ECUDA, NSG_ESTEPCAP, NSG_EDEGREE, NSG_EIO, NSG_EFORMAT = (
     0, -1, -2, -3, -4, -5, -6, -7)
-PREC_F32, PREC_BF16, PREC_FP8 = 0, 1, 2
+PREC_F32, PREC_BF16, PREC_FP8, PREC_U8 = 0, 1, 2, 3
 
 
 class NsgError(RuntimeError):
@@ -51,7 +51,8 @@ class IndexInfo(C.Structure):
                 ("device_bytes", C.c_int64), ("has_bf16", C.c_int32), ("has_fp8", C.c_int32),
                 ("fp8_scale", C.c_float), ("ms_knn", C.c_float), ("ms_centroid_nav", C.c_float),
                 ("ms_collect", C.c_float), ("ms_prune", C.c_float), ("ms_connect", C.c_float),
-                ("ms_total", C.c_float), ("n_fixup_searches", C.c_int64)]
+                ("ms_total", C.c_float), ("n_fixup_searches", C.c_int64), ("has_u8", C.c_int32),
+                ("u8_lo", C.c_float), ("u8_scale", C.c_float)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -21,11 +21,12 @@ struct nsg_index {
     int *adj = nullptr;     // [n][R], -1 padded
     int *deg = nullptr;     // [n]
     int *flag = nullptr;    // [4] device scratch for nsg_search's cap check
-    // low-precision copies, indexed by nsg_precision (1 = BF16, 2 = FP8-e4m3)
-    void *lowp[3] = {nullptr, nullptr, nullptr};
-    int lowp_dpl[3] = {0, 0, 0};        // values per row (16-byte multiple)
-    float lowp_scale[3] = {1, 1, 1};    // query multiplier
-    int lowp_exact[3] = {0, 0, 0};      // every value survived the conversion
+    // low-precision copies, indexed by nsg_precision (1 = BF16, 2 = FP8-e4m3, 3 = U8)
+    void *lowp[4] = {nullptr, nullptr, nullptr, nullptr};  // by nsg_precision
+    int lowp_dpl[4] = {0, 0, 0, 0};         // values per row (16-byte multiple)
+    float lowp_scale[4] = {1, 1, 1, 1};     // query multiplier
+    float lowp_lo[4] = {0, 0, 0, 0};        // U8 offset
+    int lowp_exact[4] = {0, 0, 0, 0};       // every value (U8: every distance) survived
     int max_degree = 0;
     double avg_degree = 0.0;
     int64_t n_fixup = 0;
@@ -616,7 +617,7 @@ nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t n
     if (nq > 0 && (!queries_dev || !ids_dev)) return NSG_EINVAL;
     nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0};
     if (params) p = *params;
-    if (p.precision < NSG_PREC_F32 || p.precision > NSG_PREC_FP8) return NSG_EINVAL;
+    if (p.precision < NSG_PREC_F32 || p.precision > NSG_PREC_U8) return NSG_EINVAL;
     if (p.precision != NSG_PREC_F32 && !idx->lowp[p.precision]) return NSG_EINVAL;  // nsg_index_prepare first
     if (p.hash_slots > 0 && (p.hash_slots < 64 || (p.hash_slots & (p.hash_slots - 1)) || p.hash_slots > 65536))
         return NSG_EINVAL;
@@ -652,8 +653,12 @@ nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t n
         l.lowp = idx->lowp[p.precision];
         l.lowp_chunks = idx->lowp_dpl[p.precision] * (p.precision == NSG_PREC_BF16 ? 2 : 1) / 16;
         l.lowp_scale = idx->lowp_scale[p.precision];
-        // auto: re-rank unless the copy holds every value exactly (then its keys are the FP32 keys)
-        l.rerank = p.rerank < 0 ? !idx->lowp_exact[p.precision] : p.rerank != 0;
+        l.lowp_lo = idx->lowp_lo[p.precision];
+        // auto: re-rank unless the copy holds every value exactly (then its keys
+        // are the FP32 keys); an exact U8 copy still re-ranks a query whose
+        // values the 8-bit map rounds
+        const int exact = idx->lowp_exact[p.precision];
+        l.rerank = p.rerank < 0 ? (!exact ? 1 : (p.precision == NSG_PREC_U8 ? 2 : 0)) : (p.rerank != 0);
     }
     return NSG_OK;
 }
@@ -871,35 +876,52 @@ nsg_status nsg_stop_train(const float *feat_dev, const uint8_t *flag_dev, const 
 }
 
 nsg_status nsg_index_prepare(nsg_index *idx, int32_t precision, void *stream) {
-    if (!idx || (precision != NSG_PREC_BF16 && precision != NSG_PREC_FP8)) return NSG_EINVAL;
+    if (!idx || precision < NSG_PREC_BF16 || precision > NSG_PREC_U8) return NSG_EINVAL;
     if (idx->lowp[precision]) return NSG_OK;
     cudaStream_t st = S(stream);
     const int epc = precision == NSG_PREC_BF16 ? 8 : 16;  // values per 16-byte chunk
     const int dpl = (idx->d + epc - 1) / epc * epc;
-    float scale = 1.0f;
-    DevBuf<int> flags;
-    NSG_CK(flags.alloc(2));
-    NSG_CK(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), st));
+    float scale = 1.0f, lo = 0.0f;
+    bool exact_map = true;  // U8: the map is x - lo (integer data of span <= 255)
+    DevBuf<unsigned> flags;
+    NSG_CK(flags.alloc(4));
+    NSG_CK(cudaMemsetAsync(flags.p, 0, 4 * sizeof(unsigned), st));
     if (precision == NSG_PREC_FP8) {  // per-tensor scale: the largest |x| maps to 448 (e4m3 max)
         unsigned bits = 0;
-        NSG_CK(nsg::launch_absmax(idx->base, idx->n * idx->dp, reinterpret_cast<unsigned *>(flags.p), st));
+        NSG_CK(nsg::launch_absmax(idx->base, idx->n * idx->dp, flags.p, st));
         NSG_CK(cudaMemcpyAsync(&bits, flags.p, sizeof(bits), cudaMemcpyDeviceToHost, st));
         NSG_CK(cudaStreamSynchronize(st));
         float mx;
         std::memcpy(&mx, &bits, sizeof(mx));
         scale = mx > 0.0f ? 448.0f / mx : 1.0f;
-        NSG_CK(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), st));
+        NSG_CK(cudaMemsetAsync(flags.p, 0, 4 * sizeof(unsigned), st));
+    } else if (precision == NSG_PREC_U8) {  // affine map of [min, max] onto 0..255
+        unsigned mm[3] = {0xffffffffu, 0u, 0u};
+        NSG_CK(cudaMemcpyAsync(flags.p, mm, sizeof(mm), cudaMemcpyHostToDevice, st));
+        NSG_CK(nsg::launch_minmax(idx->base, idx->n, idx->dp, idx->d, flags.p, st));
+        NSG_CK(cudaMemcpyAsync(mm, flags.p, sizeof(mm), cudaMemcpyDeviceToHost, st));
+        NSG_CK(cudaStreamSynchronize(st));
+        const float mn = nsg::float_from_order_key(mm[0]), mx = nsg::float_from_order_key(mm[1]);
+        const double span = (double)mx - (double)mn;
+        lo = mn;
+        exact_map = mm[2] == 0 && span <= 255.0;
+        scale = exact_map || !(span > 0.0) ? 1.0f : (float)(255.0 / span);
+        NSG_CK(cudaMemsetAsync(flags.p, 0, 4 * sizeof(unsigned), st));
     }
     DevBuf<unsigned char> buf;
     NSG_CK(buf.alloc((size_t)idx->n * dpl * (precision == NSG_PREC_BF16 ? 2 : 1)));
-    NSG_CK(nsg::launch_to_lowp(idx->base, idx->n, idx->dp, idx->d, precision, scale, buf.p, dpl, flags.p, st));
+    NSG_CK(nsg::launch_to_lowp(idx->base, idx->n, idx->dp, idx->d, precision, scale, lo, buf.p, dpl,
+                               reinterpret_cast<int *>(flags.p), st));
     int inexact = 0;
     NSG_CK(cudaMemcpyAsync(&inexact, flags.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     NSG_CK(cudaStreamSynchronize(st));
     idx->lowp[precision] = buf.release();
     idx->lowp_dpl[precision] = dpl;
     idx->lowp_scale[precision] = scale;
-    idx->lowp_exact[precision] = !inexact;
+    idx->lowp_lo[precision] = lo;
+    // U8 keys are exact only when the integer sum fits FP32 exactly: d * 255^2 < 2^24
+    idx->lowp_exact[precision] =
+        !inexact && (precision != NSG_PREC_U8 || (exact_map && (int64_t)idx->d * 65025 < (1 << 24)));
     return NSG_OK;
 }
 
@@ -962,7 +984,10 @@ nsg_status nsg_index_info(const nsg_index *idx, nsg_index_info_t *info) {
     info->has_fp8 = idx->lowp[NSG_PREC_FP8] ? (idx->lowp_exact[NSG_PREC_FP8] ? 2 : 1) : 0;
     info->fp8_scale = idx->lowp[NSG_PREC_FP8] ? idx->lowp_scale[NSG_PREC_FP8] : 0.0f;
     info->n_fixup_searches = idx->n_fixup_searches;
-    for (int p = 1; p <= 2; ++p)
+    info->has_u8 = idx->lowp[NSG_PREC_U8] ? (idx->lowp_exact[NSG_PREC_U8] ? 2 : 1) : 0;
+    info->u8_lo = idx->lowp[NSG_PREC_U8] ? idx->lowp_lo[NSG_PREC_U8] : 0.0f;
+    info->u8_scale = idx->lowp[NSG_PREC_U8] ? idx->lowp_scale[NSG_PREC_U8] : 0.0f;
+    for (int p = 1; p <= 3; ++p)
         if (idx->lowp[p]) info->device_bytes += (int64_t)idx->n * idx->lowp_dpl[p] * (p == 1 ? 2 : 1);
     info->ms_knn = idx->ms[0];
     info->ms_centroid_nav = idx->ms[1];

@@ -114,28 +114,91 @@ __device__ __forceinline__ void rows_dist(const RowQuery<G, V> &Q, const float4 
     __syncwarp();
 }
 
+// L2 prefetch of the 128-byte lines of rows ids[0..m) (row_bytes each): the
+// lanes split the (row, line) pairs.  Issued before a gather that takes
+// several rounds, it lets the later rounds hit L2 instead of HBM.
+__device__ __forceinline__ void prefetch_rows_l2(const void *base, int row_bytes, const int *ids, int m) {
+    const int lines = (row_bytes + 127) >> 7;
+    const int total = m * lines;
+    for (int x = lane_id(); x < total; x += 32) {
+        const int r = x / lines, l = x - r * lines;
+        const char *p = static_cast<const char *>(base) + (int64_t)ids[r] * row_bytes + (l << 7);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    }
+}
+
 // ---------------------------------------------------------------------------
-// Visited set: open addressing over `mask+1` slots of full 32-bit ids, so it
-// never reports a node it has not seen.  When a probe run is full the home
-// slot is overwritten and the old id is forgotten; a forgotten node may have
-// its distance computed again, which yields the identical key (dropped as a
-// duplicate by warp_merge, or rejected by the pool tail), so results do not
-// change -- only the distance count grows.
+// Visited set of full 32-bit ids, so it never reports a node it has not seen.
+// It may forget one: a forgotten node has its distance computed again, which
+// yields the identical key (dropped as a duplicate by warp_merge, or rejected
+// by the pool tail), so results do not change -- only the distance count grows.
+//
+// NSG_HASH_WAYS = 4 (default): slots/4 buckets of 4 ids (one 16-byte word),
+// probed in order from the home bucket, at most HASH_BUCKET_PROBES buckets;
+// a lookup is one 16-byte shared load per bucket.  An id is claimed into the
+// first empty slot of the first bucket that has one (compare-and-swap, so
+// lanes of one warp inserting into one bucket at once all keep their ids);
+// when every probed bucket is full it is shifted into the home bucket (the
+// bucket's oldest id is forgotten).  A bucket never becomes non-full again,
+// so a lookup may stop at the first bucket with an empty slot.  Two lanes
+// offering one id at once (a row listing it twice): the compare-and-swap
+// gives it to one of them; on the overwrite path both may report it new, and
+// warp_merge drops the second copy.
+// NSG_HASH_WAYS = 0: linear probing over single slots with compare-and-swap,
+// 8 probes, then the home slot is overwritten.
 // ---------------------------------------------------------------------------
+#ifndef NSG_HASH_WAYS
+#define NSG_HASH_WAYS 4
+#endif
 constexpr int HASH_PROBES = 8;
+constexpr int HASH_BUCKET_PROBES = 4;
+
+__device__ __forceinline__ uint4 lds_volatile_u4(const uint4 *p) {
+    uint4 v;
+    asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return v;
+}
 
 __device__ __forceinline__ bool visit(uint32_t *h, uint32_t mask, int shift, int id) {
-    uint32_t home = ((uint32_t)id * 2654435761u) >> shift;
+    const uint32_t u = (uint32_t)id;
+#if NSG_HASH_WAYS == 4
+    const uint32_t bmask = mask >> 2;  // buckets - 1
+    const uint32_t home = (u * 2654435761u) >> (shift + 2);
+    uint4 *b4 = reinterpret_cast<uint4 *>(h);
+    uint32_t b = home;
+    uint4 e0 = make_uint4(0, 0, 0, 0);
+#pragma unroll 1
+    for (int t = 0; t < HASH_BUCKET_PROBES; ++t) {
+#pragma unroll 1
+        for (int tries = 0; tries < 4; ++tries) {  // each failed claim fills one more slot
+            const uint4 e = lds_volatile_u4(b4 + b);
+            if (t == 0) e0 = e;
+            if (e.x == u || e.y == u || e.z == u || e.w == u) return false;
+            const int j = e.x == HASH_EMPTY ? 0 : e.y == HASH_EMPTY ? 1 : e.z == HASH_EMPTY ? 2 : e.w == HASH_EMPTY ? 3 : -1;
+            if (j < 0) break;  // full: next bucket
+            const uint32_t old = atomicCAS(h + b * 4 + j, HASH_EMPTY, u);
+            if (old == HASH_EMPTY) return true;
+            if (old == u) return false;
+        }
+        b = (b + 1) & bmask;
+    }
+    b4[home] = make_uint4(u, e0.x, e0.y, e0.z);
+    return true;
+#else
+    uint32_t home = (u * 2654435761u) >> shift;
     uint32_t s = home;
 #pragma unroll 1
     for (int t = 0; t < HASH_PROBES; ++t) {
-        uint32_t old = atomicCAS(&h[s], HASH_EMPTY, (uint32_t)id);
+        uint32_t old = atomicCAS(&h[s], HASH_EMPTY, u);
         if (old == HASH_EMPTY) return true;
-        if (old == (uint32_t)id) return false;
+        if (old == u) return false;
         s = (s + 1) & mask;
     }
-    atomicExch(&h[home], (uint32_t)id);
+    atomicExch(&h[home], u);
     return true;
+#endif
 }
 
 __device__ __forceinline__ void hash_clear(uint32_t *h, int slots) {
@@ -148,10 +211,11 @@ __device__ __forceinline__ void hash_clear(uint32_t *h, int slots) {
 // ---------------------------------------------------------------------------
 // warp_merge: merge m candidate keys cand[0..m) into the sorted list
 // list[0..size) of capacity cap ("add, sort ascending, keep the first cap").
-// Candidates not below the tail of a full list, and candidates equal to a
-// list entry (checked flag ignored), are dropped, and so is id `excl`.  Scratch ck/sk (u64) and
-// cp/sp (int) need m entries each.  Returns the smallest position written
-// (cap when nothing entered).  All 32 lanes must call it.
+// Candidates not below the tail of a full list, candidates equal to a list
+// entry (checked flag ignored) or to an earlier candidate, and id `excl` are
+// dropped.  Scratch ck/sk (u64) and cp/sp (int) need m entries each.  Returns
+// the smallest position written (cap when nothing entered).  All 32 lanes
+// must call it.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int lower_bound_key(const uint64_t *list, int size, uint64_t k) {
     int lo = 0, hi = size;
@@ -203,17 +267,46 @@ __device__ __forceinline__ int warp_merge(uint64_t *list, int cap, int &size, co
     __syncwarp();
     if (nk == 0) return cap;
     // rank among the kept candidates (stable on equal keys)
+    bool dup = false;
     for (int j = lane; j < nk; j += 32) {
         uint64_t k = ck[j];
         int r = 0;
         for (int i = 0; i < nk; ++i) {
             uint64_t o = ck[i];
-            r += (o < k) || (o == k && i < j);
+            const bool same_before = o == k && i < j;
+            r += (o < k) || same_before;
+            dup |= same_before;
         }
         sk[r] = k;
         sp[r] = cp[j];
     }
     __syncwarp();
+    if (__any_sync(NSG_FULL, dup)) {
+        // one node offered twice in this batch (a row that lists an id twice):
+        // equal keys sit next to each other in sk; keep the first of each run
+        int w = 0;
+        for (int b = 0; b < nk; b += 32) {
+            const int j = b + (int)lane;
+            uint64_t k = 0;
+            int p = 0;
+            bool keep = false;
+            if (j < nk) {
+                k = sk[j];
+                p = sp[j];
+                keep = j == 0 || sk[j - 1] != k;
+            }
+            const unsigned bal = __ballot_sync(NSG_FULL, keep);
+            __syncwarp();
+            if (keep) {
+                const int o = w + __popc(bal & lanemask_lt());
+                sk[o] = k;
+                sp[o] = p;
+            }
+            w += __popc(bal);
+            __syncwarp();
+        }
+        nk = w;
+    }
     const int lo = sp[0];
     // move old entries i >= lo to i + #{r : sp[r] <= i}, top chunk first
     for (int c = ((size - 1) >> 5) << 5; c >= (lo & ~31); c -= 32) {

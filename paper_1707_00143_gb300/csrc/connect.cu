@@ -11,12 +11,18 @@
 //   speculate  one warp per listed u runs Alg. 1 on the graph as it stands and
 //              keeps its final pool plus the ids it expanded;
 //   commit     one CTA walks the list in order: skip u if an earlier fix-up of
-//              this batch reached it; reuse its pool unless a node it expanded
-//              gained an edge since the snapshot (then search again on the
+//              this batch reached it; reuse its pool unless an edge added since
+//              the snapshot could have changed it (then search again on the
 //              current graph); pick s from the pool with the current degrees;
 //              append s->u; mark what u reaches.
-// Alg. 1 reads only the adjacency rows of the nodes it expands, so an
-// unchanged expanded set means an unchanged pool.  The list holds consecutive
+// Alg. 1 reads only the adjacency rows of the nodes it expands, and a new
+// edge e->w matters only if e was expanded and w would have entered the pool
+// then: the pool was not yet full, or key(w) was below its L-th key at that
+// expansion.  Once the pool is full its L-th key never rises, so a w that
+// could not enter at e's expansion can never enter later either, and the
+// pool is unchanged.  The speculative search logs, per expansion, the node
+// and that entry bar; the check uses a relative slack of 2^-10 on the
+// distance, so summation-order rounding can only cause an extra re-search.  The list holds consecutive
 // unreached ids, so walking it in order and skipping reached ones visits the
 // same u sequence as "smallest unreached id" after every fix-up.
 #include <climits>
@@ -24,6 +30,12 @@
 
 #include "kernels.h"
 #include "search_core.cuh"
+
+// Unreached ids speculated per batch: larger batches run more searches in
+// parallel, smaller ones leave fewer earlier fix-ups to make a speculation stale.
+#ifndef NSG_CONNECT_BATCH
+#define NSG_CONNECT_BATCH 64
+#endif
 
 namespace nsg {
 
@@ -105,6 +117,7 @@ struct SpecArgs {
     uint64_t *pools;  // [B][L]
     int *psize;       // [B]
     int *xlog;        // [B][xcap]
+    uint64_t *xthr;   // [B][xcap]: entry bar of the pool at each expansion
     int *xcnt;        // [B]: expansions, INT_MAX when the search hit its cap
     int xcap;
 };
@@ -123,7 +136,7 @@ __global__ void __launch_bounds__(256) speculate_kernel(SpecArgs a) {
         dist.Q.load_row(a.base4 + (int64_t)u * a.dp4, a.dp4);
         SearchOut o = warp_alg1<false, false>(dist, GraphRef{a.adj, a.R}, a.nav, a.L, s, (uint32_t)a.H - 1,
                                               a.hshift, a.max_steps, -1, 0, csize, a.xlog + (int64_t)j * a.xcap,
-                                              a.xcap);
+                                              a.xcap, nullptr, a.xthr + (int64_t)j * a.xcap);
         for (int t = lane; t < a.L; t += 32) a.pools[(int64_t)j * a.L + t] = t < o.size ? s.pool[t] : KEY_INF;
         if (lane == 0) {
             a.psize[j] = o.size;
@@ -140,9 +153,10 @@ struct CommitArgs {
     int *adj, *deg;
     int R, W, nav, L, H, hshift, max_steps;
     uint32_t *reached, *dirty;
+    int *deg0;  // out-degree at the start of the batch, valid where dirty
     int *queue;
     const int *list, *meta;
-    const uint64_t *pools;
+    const uint64_t *pools, *xthr;
     const int *psize, *xlog, *xcnt;
     int xcap;
     int *out;  // [0] edges added, [1] status, [2] capped, [3] re-searched
@@ -165,8 +179,29 @@ __global__ void __launch_bounds__(256) commit_kernel(CommitArgs a) {
         if (xc > a.xcap) {
             if (tid == 0) sh_flag = 1;
         } else {
-            for (int t = tid; t < xc; t += blockDim.x)
-                if (bit_is_set(a.dirty, a.xlog[(int64_t)i * a.xcap + t])) sh_flag = 1;
+            const float4 *xu = a.base4 + (int64_t)u * a.dp4;
+            for (int t = tid; t < xc; t += blockDim.x) {
+                const int e = a.xlog[(int64_t)i * a.xcap + t];
+                if (!bit_is_set(a.dirty, e)) continue;
+                const uint64_t thr = a.xthr[(int64_t)i * a.xcap + t];
+                if (thr == KEY_INF) {  // the pool was not full: any new neighbour entered
+                    sh_flag = 1;
+                    continue;
+                }
+                const float bar = kd2(thr) * (1.0f + 1.0f / 1024.0f);
+                const int d1 = ldv(a.deg + e);
+                for (int j = ldv(a.deg0 + e); j < d1; ++j) {
+                    const int w = ldv(a.adj + (int64_t)e * a.R + j);
+                    const float4 *xw = a.base4 + (int64_t)w * a.dp4;
+                    float d2 = 0.0f;
+                    for (int c = 0; c < a.dp4; ++c) {
+                        const float4 p = xu[c], q = xw[c];
+                        const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z, dw = p.w - q.w;
+                        d2 += dx * dx + dy * dy + dz * dz + dw * dw;
+                    }
+                    if (d2 <= bar) sh_flag = 1;
+                }
+            }
         }
         __syncthreads();
         const uint64_t *pool;
@@ -217,7 +252,7 @@ __global__ void __launch_bounds__(256) commit_kernel(CommitArgs a) {
             const int dg = a.deg[sel];
             a.adj[(int64_t)sel * a.R + dg] = u;
             a.deg[sel] = dg + 1;
-            atomicOr(a.dirty + (sel >> 5), 1u << (sel & 31));
+            if (!(atomicOr(a.dirty + (sel >> 5), 1u << (sel & 31)) & (1u << (sel & 31)))) a.deg0[sel] = dg;
             atomicOr(a.reached + (u >> 5), 1u << (u & 31));
             a.queue[0] = u;
             sh_qtail = 1;
@@ -263,16 +298,16 @@ struct Buf {
 cudaError_t run_connect(const ConnectLaunch &l, int out_host[4], cudaStream_t st) {
     const int64_t n = l.n;
     const int64_t nwords = (n + 31) / 32;
-    const int B = 4096;
+    const int B = NSG_CONNECT_BATCH;
     const int xcap = 4 * l.L + 64;
     Buf<uint32_t> reached, dirty;
-    Buf<int> qa, qb, cnt, list, meta, psize, xlog, xcnt, out;
-    Buf<uint64_t> pools;
+    Buf<int> qa, qb, cnt, list, meta, psize, xlog, xcnt, out, deg0;
+    Buf<uint64_t> pools, xthr;
     cudaError_t e;
     if ((e = reached.alloc(nwords)) || (e = dirty.alloc(nwords)) || (e = qa.alloc(n)) || (e = qb.alloc(n)) ||
         (e = cnt.alloc(2)) || (e = list.alloc(B)) || (e = meta.alloc(2)) || (e = psize.alloc(B)) ||
         (e = xlog.alloc((size_t)B * xcap)) || (e = xcnt.alloc(B)) || (e = out.alloc(4)) ||
-        (e = pools.alloc((size_t)B * l.L)))
+        (e = pools.alloc((size_t)B * l.L)) || (e = xthr.alloc((size_t)B * xcap)) || (e = deg0.alloc(n)))
         return e;
     if ((e = cudaMemsetAsync(reached.p, 0, nwords * 4, st)) || (e = cudaMemsetAsync(out.p, 0, 16, st))) return e;
     // reach from the navigating node: level-synchronous BFS
@@ -302,6 +337,7 @@ cudaError_t run_connect(const ConnectLaunch &l, int out_host[4], cudaStream_t st
     sa.pools = pools.p;
     sa.psize = psize.p;
     sa.xlog = xlog.p;
+    sa.xthr = xthr.p;
     sa.xcnt = xcnt.p;
     sa.xcap = xcap;
     CommitArgs ca;
@@ -319,12 +355,14 @@ cudaError_t run_connect(const ConnectLaunch &l, int out_host[4], cudaStream_t st
     ca.max_steps = l.max_steps;
     ca.reached = reached.p;
     ca.dirty = dirty.p;
+    ca.deg0 = deg0.p;
     ca.queue = qa.p;
     ca.list = list.p;
     ca.meta = meta.p;
     ca.pools = pools.p;
     ca.psize = psize.p;
     ca.xlog = xlog.p;
+    ca.xthr = xthr.p;
     ca.xcnt = xcnt.p;
     ca.xcap = xcap;
     ca.out = out.p;

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace nsg {
 
@@ -26,11 +27,12 @@ struct SearchLaunch {
     int *n_expand, *n_dist, *status;
     int *any_capped;  // device flag, nullable
     // precision forms: traversal on a BF16 / FP8 copy, FP32 re-rank of the pool
-    int precision = 0;  // 0 FP32, 1 BF16, 2 FP8-e4m3
+    int precision = 0;  // 0 FP32, 1 BF16, 2 FP8-e4m3, 3 U8
     const void *lowp = nullptr;
     int lowp_chunks = 0;  // 16-byte chunks per low-precision row
     float lowp_scale = 1.0f;
-    int rerank = 0;
+    float lowp_lo = 0.0f;  // U8: offset of the 8-bit map
+    int rerank = 0;        // 1: always; U8 with 2: only queries the 8-bit map rounds
     // learned early termination (FP16 MLP parameters, nullptr = none) and traces
     const void *stop_model = nullptr;
     float stop_logit = 0.0f;
@@ -56,10 +58,21 @@ cudaError_t run_stop_train(const float *feat, const unsigned char *flag, const i
 
 // Largest |x| over `count` floats (bits of a non-negative float, atomicMax).
 cudaError_t launch_absmax(const float *x, int64_t count, unsigned *out_bits, cudaStream_t st);
-// [n][dp] FP32 -> [n][dpl] BF16 (precision 1) or FP8-e4m3 of x*scale (precision 2),
-// zero padded; *inexact is raised when some value does not survive the round trip.
-cudaError_t launch_to_lowp(const float *src, int64_t n, int dp, int d, int precision, float scale, void *dst,
-                           int dpl, int *inexact, cudaStream_t st);
+// Order-preserving keys of min x and max x (out[0], out[1]; start them at
+// 0xffffffff and 0) and out[2] |= 1 when some x is not an integer.
+cudaError_t launch_minmax(const float *x, int64_t n, int dp, int d, unsigned *out, cudaStream_t st);
+// (key of f: sign bit set -> all bits flipped, else the sign bit set)
+inline float float_from_order_key(unsigned k) {
+    unsigned b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+}
+// [n][dp] FP32 -> [n][dpl] BF16 (precision 1), FP8-e4m3 of x*scale (precision 2)
+// or U8 of clamp(rint((x - lo) * scale), 0, 255) (precision 3), zero padded;
+// *inexact is raised when some value does not survive the round trip.
+cudaError_t launch_to_lowp(const float *src, int64_t n, int dp, int d, int precision, float scale, float lo,
+                           void *dst, int dpl, int *inexact, cudaStream_t st);
 
 // Search-and-collect on the kNN graph for nodes v0..v0+nv-1.
 struct CollectLaunch {

@@ -14,11 +14,15 @@
 // of base tiles), warp 1 owns TMEM and issues the MMAs into two accumulator
 // buffers, warps 2-5 are the epilogue: thread r holds query row r's running
 // top-k.  A base column j enters row r's candidate buffer only when
-// |x_j|^2 - 2 q.x_j < (current k-th distance) - |q|^2 (one FMA + one compare
-// per element); columns arrive in increasing id, so a strict comparison on the
+// |x_j|^2 - 2 q.x_j < (current k-th distance) - |q|^2; the common case costs
+// one FMA and one min per element (a group of 16 columns is tested through its
+// minimum).  Columns arrive in increasing id, so a strict comparison on the
 // distance alone implements the (distance, id) order.  Buffers of 16+ keys are
 // merged warp-cooperatively into the row's sorted list, which lives in the
 // output arrays.
+#include <algorithm>
+#include <cstdlib>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -43,10 +47,13 @@ struct TcArgs {
     const float *qn;  // [m] squared norms of the query rows
     const float *xn;  // [ntiles * 128] squared norms of the base rows
     int64_t m, n, q0;
-    int self_join, KL, ntiles;
+    int self_join, KL;
+    int t0, t1;       // base tiles [t0, t1) of this launch (one chunk of the base)
+    int first, last;  // first chunk: lists start empty; last chunk: pad short lists
     int kb;  // 64-wide K chunks per row (streaming form)
     int *ids;
     float *d2;
+    int *lsz;  // [m] list sizes carried between chunks
     int *err;
 };
 
@@ -198,9 +205,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tc::tma_load_2d(sA + kb * (TC_M * 128), &tmA, a_full, kb * TC_BOXK, (int)row0);
             }
             const int per_tile = DK ? 1 : a.kb;  // stages per tile
+            const int nt = a.t1 - a.t0;
             int issued = 0;
-            for (int c = 0; c < a.ntiles * per_tile; ++c) {
-                const int s = c % Cfg::NS, t = c / per_tile, kc = c - t * per_tile;
+            for (int c = 0; c < nt * per_tile; ++c) {
+                const int s = c % Cfg::NS, tl = c / per_tile, kc = c - tl * per_tile, t = a.t0 + tl;
                 if (!tc::mbar_wait(b_empty + s, ((c / Cfg::NS) & 1) ^ 1, abort, gerr)) break;
                 tc::mbar_expect_tx(b_full + s, Cfg::B_BYTES);
                 unsigned char *dst = sB + s * Cfg::B_BYTES;
@@ -231,7 +239,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             bool ok = DK ? tc::mbar_wait(a_full, 0, abort, gerr) : true;
             const int per_tile = DK ? 1 : a.kb;
             int c = 0;
-            for (int t = 0; ok && t < a.ntiles; ++t) {
+            for (int t = 0; ok && t < a.t1 - a.t0; ++t) {  // local tile index
                 const int buf = t & 1;
                 if (!tc::mbar_wait(acc_empty + buf, ((t >> 1) & 1) ^ 1, abort, gerr)) break;
                 tc::fence_after_sync();
@@ -283,16 +291,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const float qn_r = valid ? a.qn[row_g] : 0.0f;
         const int64_t self_id = a.self_join ? a.q0 + row_g : -1;
         uint64_t *mybuf = bufs + row_local * TC_BUF;
-        int cnt = 0, lsize = 0;
-        float thrp = __int_as_float(0x7f800000);
+        // the row's list (size and k-th key) carried over from earlier chunks;
+        // a row past the end takes nothing: its threshold is -inf
+        int cnt = 0, lsize = valid && !a.first ? a.lsz[row_g] : 0;
+        float thrp = __int_as_float(valid ? 0x7f800000 : 0xff800000);
+        if (valid && lsize == a.KL) thrp = a.d2[row_g * a.KL + a.KL - 1] - qn_r;
         const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
         bool ok = true;
-        for (int t = 0; t < a.ntiles; ++t) {
-            const int buf = t & 1;
+        const float4 *xn4 = reinterpret_cast<const float4 *>(a.xn);
+        float4 xnext = __ldg(xn4 + (int64_t)a.t0 * (TC_N / 4) + lane);  // norms one tile ahead
+        for (int tl = 0; tl < a.t1 - a.t0; ++tl) {
+            const int buf = tl & 1, t = a.t0 + tl;
             const int64_t col0 = (int64_t)t * TC_N;
-            reinterpret_cast<float4 *>(xs)[lane] = __ldg(reinterpret_cast<const float4 *>(a.xn + col0) + lane);
+            // columns jj < lim exist; jj == self_local is the row itself
+            const int lim = a.n - col0 < TC_N ? (int)(a.n - col0) : TC_N;
+            const int self_local = self_id >= col0 && self_id < col0 + TC_N ? (int)(self_id - col0) : -1;
             __syncwarp();
-            const bool got = tc::mbar_wait(acc_full + buf, (t >> 1) & 1, abort, gerr);
+            reinterpret_cast<float4 *>(xs)[lane] = xnext;
+            if (t + 1 < a.t1) xnext = __ldg(xn4 + (int64_t)(t + 1) * (TC_N / 4) + lane);
+            __syncwarp();
+            const bool got = tc::mbar_wait(acc_full + buf, (tl >> 1) & 1, abort, gerr);
             if (!__all_sync(NSG_FULL, got)) {  // warp-uniform before the .sync.aligned TMEM loads
                 ok = false;
                 break;
@@ -310,14 +328,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
+                    // |x|^2 - 2 q.x for 16 columns and their minimum: one FMA
+                    // and one min per element; the insertion path runs only
+                    // when some column beats the row's current k-th distance
+                    const int jb = c * 32 + h * 16;
+                    const float4 *x4 = reinterpret_cast<const float4 *>(xs + jb);
+                    float tv[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int jj = c * 32 + h * 16 + j;
-                        const float tv = fmaf(-2.0f, __uint_as_float(v[h * 16 + j]), xs[jj]);
-                        const int64_t col = col0 + jj;
-                        if (valid && tv < thrp && col < a.n && col != self_id) {
-                            mybuf[cnt] = make_key(fmaxf(qn_r + tv, 0.0f), (int)col);
-                            ++cnt;
+                    for (int j4 = 0; j4 < 4; ++j4) {
+                        const float4 xv = x4[j4];
+                        const float xa[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            tv[j4 * 4 + e] = fmaf(-2.0f, __uint_as_float(v[h * 16 + j4 * 4 + e]), xa[e]);
+                    }
+                    float m8[8];  // minimum as a tree (independent instructions)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) m8[j] = fminf(tv[2 * j], tv[2 * j + 1]);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) m8[j] = fminf(m8[2 * j], m8[2 * j + 1]);
+                    const float mn = fminf(fminf(m8[0], m8[1]), fminf(m8[2], m8[3]));
+                    if (mn < thrp) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int jj = jb + j;
+                            if (tv[j] < thrp && jj < lim && jj != self_local) {
+                                mybuf[cnt] = make_key(fmaxf(qn_r + tv[j], 0.0f), (int)(col0 + jj));
+                                ++cnt;
+                            }
                         }
                     }
                     unsigned need = __ballot_sync(NSG_FULL, cnt >= TC_MERGE_AT);
@@ -338,7 +376,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 merge_row(src, row_local, row_g, cnt, lsize, thrp, qn_r, bufs, ls, sb, thr_slot, a.ids,
                           a.d2, a.KL);
             }
-            // pad rows holding fewer than k candidates
+            if (!a.last) {  // carry the list size to the next chunk
+                if (valid) a.lsz[row_g] = lsize;
+            } else  // pad rows holding fewer than k candidates
             for (int src = 0; src < 32; ++src) {
                 const int s = __shfl_sync(NSG_FULL, lsize, src);
                 const int64_t rg = __shfl_sync(NSG_FULL, row_g, src);
@@ -487,32 +527,49 @@ cudaError_t launch_knn_tc(const KnnLaunch &l, int *used, cudaStream_t st) {
     a.q0 = l.q0;
     a.self_join = l.self_join;
     a.KL = KL;
-    a.ntiles = (int)ntiles;
     a.kb = dk / TC_BOXK;
     a.ids = idsout;
     a.d2 = d2out;
     a.err = flag.p + 1;
+    // The base is taken in chunks of ~48 MB of BF16 rows, one launch per chunk
+    // over every query tile, so a chunk stays in L2 while all query tiles pass
+    // over it (a single sweep per CTA would re-read a base larger than L2 from
+    // HBM once per wave of CTAs).  Rows see columns in increasing id across
+    // chunks, and their lists carry over through the output arrays and lsz.
+    int64_t chunk_tiles = std::max<int64_t>(1, (int64_t(48) << 20) / ((int64_t)TC_N * dk * 2));
+    if (const char *ct = getenv("NSG_KNN_CHUNK_TILES"))  // smaller chunks (tests)
+        if (atoi(ct) > 0) chunk_tiles = atoi(ct);
+    const int64_t nchunks = (ntiles + chunk_tiles - 1) / chunk_tiles;
+    Scratch<int> lsz;
+    if (nchunks > 1 && (e = lsz.alloc((size_t)l.nq)) != cudaSuccess) return e;
+    a.lsz = lsz.p;
     const int64_t grid = (l.nq + TC_M - 1) / TC_M;
-    if (dk == 64) {
-        auto kern = knn_tc_kernel<64>;
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<64>::SMEM)) !=
-            cudaSuccess)
-            return e;
-        kern<<<(unsigned)grid, TC_THREADS, TcCfg<64>::SMEM, st>>>(mA, mB, a);
-    } else if (dk == 128) {
-        auto kern = knn_tc_kernel<128>;
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<128>::SMEM)) !=
-            cudaSuccess)
-            return e;
-        kern<<<(unsigned)grid, TC_THREADS, TcCfg<128>::SMEM, st>>>(mA, mB, a);
-    } else {
-        auto kern = knn_tc_kernel<0>;
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<0>::SMEM)) !=
-            cudaSuccess)
-            return e;
-        kern<<<(unsigned)grid, TC_THREADS, TcCfg<0>::SMEM, st>>>(mA, mB, a);
+    for (int64_t c = 0; c < nchunks; ++c) {
+        a.t0 = (int)(c * chunk_tiles);
+        a.t1 = (int)std::min<int64_t>(ntiles, (c + 1) * chunk_tiles);
+        a.first = c == 0;
+        a.last = c == nchunks - 1;
+        if (dk == 64) {
+            auto kern = knn_tc_kernel<64>;
+            if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<64>::SMEM)) !=
+                cudaSuccess)
+                return e;
+            kern<<<(unsigned)grid, TC_THREADS, TcCfg<64>::SMEM, st>>>(mA, mB, a);
+        } else if (dk == 128) {
+            auto kern = knn_tc_kernel<128>;
+            if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<128>::SMEM)) !=
+                cudaSuccess)
+                return e;
+            kern<<<(unsigned)grid, TC_THREADS, TcCfg<128>::SMEM, st>>>(mA, mB, a);
+        } else {
+            auto kern = knn_tc_kernel<0>;
+            if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<0>::SMEM)) !=
+                cudaSuccess)
+                return e;
+            kern<<<(unsigned)grid, TC_THREADS, TcCfg<0>::SMEM, st>>>(mA, mB, a);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(h, flag.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
     if (h[1]) return cudaErrorLaunchTimeout;  // a pipeline wait gave up (bounded waits)

@@ -1,5 +1,5 @@
-// lowp.cu -- building the BF16 / FP8-e4m3 copies of the base used by the
-// precision forms of the search.
+// lowp.cu -- building the BF16 / FP8-e4m3 / U8 copies of the base used by
+// the precision forms of the search.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -25,9 +25,46 @@ cudaError_t launch_absmax(const float *x, int64_t count, unsigned *out_bits, cud
     return cudaGetLastError();
 }
 
+__device__ __forceinline__ unsigned order_key(float f) {
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__global__ void minmax_kernel(const float *__restrict__ x, int64_t n, int dp, int d, unsigned *out) {
+    unsigned lo = 0xffffffffu, hi = 0u;
+    bool frac = false;
+    const int64_t total = n * d;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = x[(i / d) * dp + i % d];
+        const unsigned kk = order_key(v);
+        lo = min(lo, kk);
+        hi = max(hi, kk);
+        frac |= rintf(v) != v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(NSG_FULL, lo, o));
+        hi = max(hi, __shfl_xor_sync(NSG_FULL, hi, o));
+    }
+    const bool any_frac = __any_sync(NSG_FULL, frac);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(out, lo);
+        atomicMax(out + 1, hi);
+        if (any_frac) atomicOr(out + 2, 1u);
+    }
+}
+
+cudaError_t launch_minmax(const float *x, int64_t n, int dp, int d, unsigned *out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n * d + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    minmax_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, st>>>(x, n, dp, d, out);
+    return cudaGetLastError();
+}
+
 template <int P>
-__global__ void to_lowp_kernel(const float *__restrict__ src, int64_t n, int dp, int d, float scale, void *dst,
-                               int dpl, int *inexact) {
+__global__ void to_lowp_kernel(const float *__restrict__ src, int64_t n, int dp, int d, float scale, float lo,
+                               void *dst, int dpl, int *inexact) {
     const int64_t total = n * dpl;
     bool bad = false;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
@@ -38,6 +75,11 @@ __global__ void to_lowp_kernel(const float *__restrict__ src, int64_t n, int dp,
             const __nv_bfloat16 h = __float2bfloat16_rn(v);
             reinterpret_cast<__nv_bfloat16 *>(dst)[x] = h;
             bad |= __bfloat162float(h) != v;
+        } else if (P == 3) {
+            const float y = (v - lo) * scale;
+            const float u = c < d ? fminf(fmaxf(rintf(y), 0.0f), 255.0f) : 0.0f;
+            reinterpret_cast<unsigned char *>(dst)[x] = (unsigned char)u;
+            bad |= c < d && u != y;
         } else {
             const __nv_fp8_storage_t h = __nv_cvt_float_to_fp8(v * scale, __NV_SATFINITE, __NV_E4M3);
             reinterpret_cast<__nv_fp8_storage_t *>(dst)[x] = h;
@@ -48,14 +90,15 @@ __global__ void to_lowp_kernel(const float *__restrict__ src, int64_t n, int dp,
     if (__any_sync(NSG_FULL, bad) && (threadIdx.x & 31) == 0) atomicOr(inexact, 1);
 }
 
-cudaError_t launch_to_lowp(const float *src, int64_t n, int dp, int d, int precision, float scale, void *dst,
-                           int dpl, int *inexact, cudaStream_t st) {
+cudaError_t launch_to_lowp(const float *src, int64_t n, int dp, int d, int precision, float scale, float lo,
+                           void *dst, int dpl, int *inexact, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     int64_t blocks = (n * dpl + 255) / 256;
     const int64_t cap = (int64_t)sm_count() * 16;
     const int g = (int)(blocks < cap ? blocks : cap);
-    if (precision == 1) to_lowp_kernel<1><<<g, 256, 0, st>>>(src, n, dp, d, scale, dst, dpl, inexact);
-    else to_lowp_kernel<2><<<g, 256, 0, st>>>(src, n, dp, d, scale, dst, dpl, inexact);
+    if (precision == 1) to_lowp_kernel<1><<<g, 256, 0, st>>>(src, n, dp, d, scale, lo, dst, dpl, inexact);
+    else if (precision == 2) to_lowp_kernel<2><<<g, 256, 0, st>>>(src, n, dp, d, scale, lo, dst, dpl, inexact);
+    else to_lowp_kernel<3><<<g, 256, 0, st>>>(src, n, dp, d, scale, lo, dst, dpl, inexact);
     return cudaGetLastError();
 }
 

@@ -1,8 +1,8 @@
 // lowp.cuh -- traversal distances on low-precision copies of the base.
 //
-// Rows are stored as BF16 (8 values per 16-byte chunk) or FP8-e4m3 (16 per
+// Rows are stored as BF16 (8 values per 16-byte chunk), FP8-e4m3 (16 per
 // chunk, values pre-multiplied by a per-tensor scale so the largest |x| maps
-// to 448).  The query stays FP32 (scaled the same way), each chunk is widened
+// to 448) or U8 (16 per chunk, integer arithmetic, below).  The query stays FP32 (scaled the same way), each chunk is widened
 // to FP32 and the squared differences are accumulated in FP32.  Scaling all
 // coordinates by one factor scales every squared distance by its square, so
 // the traversal order is unaffected by it.  On integer data 0..255 the BF16
@@ -17,7 +17,89 @@
 
 namespace nsg {
 
-enum { PREC_F32 = 0, PREC_BF16 = 1, PREC_FP8 = 2 };
+enum { PREC_F32 = 0, PREC_BF16 = 1, PREC_FP8 = 2, PREC_U8 = 3 };
+
+// ---------------------------------------------------------------------------
+// 8-bit integer form: x_u8 = clamp(rint((x - lo) * s), 0, 255), the query
+// quantised the same way, squared differences summed exactly in int32 with
+// __vabsdiffu4 (per-byte |a - b|) and __dp4a.  With lo = 0 and s = 1 (integer
+// data 0..255) the copy, the query and every distance are exact, so the keys
+// equal the FP32 keys while a row is a quarter of the FP32 bytes.
+// ---------------------------------------------------------------------------
+template <int G, int VC>
+struct RowQueryU8 {
+    uint4 q[VC];  // 16 quantised values per chunk
+    // Returns (warp-uniform) whether the 8-bit map kept every query value.
+    __device__ __forceinline__ bool load(const float *__restrict__ src, int d, float lo, float s) {
+        const int sub = lane_id() % G;
+        bool exact = true;
+#pragma unroll
+        for (int t = 0; t < VC; ++t) {
+            uint32_t w[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                uint32_t word = 0;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int j = (t * G + sub) * 16 + b * 4 + e;
+                    const float y = j < d ? (__ldg(src + j) - lo) * s : 0.0f;
+                    const float v = fminf(fmaxf(rintf(y), 0.0f), 255.0f);
+                    exact &= v == y;
+                    word |= (uint32_t)v << (8 * e);
+                }
+                w[b] = word;
+            }
+            q[t] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        return __all_sync(NSG_FULL, exact);
+    }
+};
+
+template <int G, int VC, int U>
+struct DistU8 {
+    RowQueryU8<G, VC> Q;
+    const uint4 *base;  // [n][dc] chunks of 16 bytes
+    int dc;
+    __device__ __forceinline__ void operator()(const int *ids, int m, uint64_t *keys) const {
+        constexpr int PG = 32 / G;
+        const int lane = lane_id(), grp = lane / G, sub = lane % G;
+        for (int c0 = 0; c0 < m; c0 += PG * U) {
+            uint4 x[U][VC];
+            int id[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int c = c0 + u * PG + grp;
+                id[u] = c < m ? ids[c] : -1;
+                const uint4 *row = base + (int64_t)(id[u] < 0 ? 0 : id[u]) * dc;
+#pragma unroll
+                for (int t = 0; t < VC; ++t) {
+                    const int k = t * G + sub;
+                    x[u][t] = (id[u] >= 0 && k < dc) ? __ldg(row + k) : make_uint4(0, 0, 0, 0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                unsigned s = 0;
+#pragma unroll
+                for (int t = 0; t < VC; ++t) {
+                    const uint32_t a[4] = {x[u][t].x, x[u][t].y, x[u][t].z, x[u][t].w};
+                    const uint32_t b[4] = {Q.q[t].x, Q.q[t].y, Q.q[t].z, Q.q[t].w};
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const unsigned df = __vabsdiffu4(a[w], b[w]);
+                        s = __dp4a(df, df, s);
+                    }
+                }
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(NSG_FULL, s, o, G);
+                const int c = c0 + u * PG + grp;
+                if (sub == 0 && c < m) keys[c] = make_key((float)s, id[u]);
+            }
+        }
+        __syncwarp();
+    }
+    __device__ __forceinline__ void prefetch(const int *, int) const {}  // measured: no gain
+};
 
 template <int P>
 struct PrecEpc;  // values per 16-byte chunk
@@ -119,6 +201,7 @@ struct DistLp {
         }
         __syncwarp();
     }
+    __device__ __forceinline__ void prefetch(const int *, int) const {}  // measured: no gain
 };
 
 }  // namespace nsg

@@ -8,19 +8,31 @@
 #include "lowp.cuh"
 #include "search_core.cuh"
 
-// Launch shape of the search kernel: minimum resident 256-thread blocks per
-// SM (bounds the registers per thread) and rows in flight per lane group on
-// the low-precision paths (1 or 2 16-byte chunks per lane).
+// Launch shape of the search kernels: minimum resident 256-thread blocks per
+// SM (bounds the registers per thread) of the plain and the low-precision
+// kernels, and rows in flight per lane group on the low-precision paths (1 or
+// 2 16-byte chunks per lane; NSG_U8ROWS for the 8-bit form).  Left unbounded
+// the low-precision kernels, which also carry the FP32 re-rank, take ~112
+// registers and half the resident warps.
 #ifdef NSG_SEARCH_MINB
 #define NSG_SEARCH_BOUNDS __launch_bounds__(256, NSG_SEARCH_MINB)
 #else
 #define NSG_SEARCH_BOUNDS __launch_bounds__(256)
+#endif
+#ifndef NSG_LOWP_MINB
+#define NSG_LOWP_MINB 4
 #endif
 #ifndef NSG_UL1
 #define NSG_UL1 2
 #endif
 #ifndef NSG_UL2
 #define NSG_UL2 2
+#endif
+#ifndef NSG_U8ROWS
+#define NSG_U8ROWS 2
+#endif
+#ifndef NSG_U8CHUNKS
+#define NSG_U8CHUNKS 2
 #endif
 
 namespace nsg {
@@ -35,10 +47,12 @@ static inline int log2i(unsigned x) {
 struct SearchArgs {
     const float4 *base4;  // FP32 rows [n][dp4] (re-rank and the plain form)
     int dp4;
-    const uint4 *lowp;  // BF16 / FP8 rows [n][dc] 16-byte chunks (precision forms)
+    const uint4 *lowp;  // BF16 / FP8 / U8 rows [n][dc] 16-byte chunks (precision forms)
     int dc;
     float scale;  // query multiplier matching the low-precision copy
-    int rerank;   // precision forms: re-rank the final pool with FP32 rows
+    float lo;     // U8: offset of the 8-bit map
+    int rerank;   // precision forms: re-rank the final pool with FP32 rows (1),
+                  // U8 only for queries the 8-bit map rounds (2)
     const int *adj;
     int width, W;
     int start;
@@ -65,9 +79,11 @@ struct SearchArgs {
 };
 
 // Alg. 1 per query.  P = PREC_F32: distances on the FP32 rows (the plain
-// form).  P = PREC_BF16 / PREC_FP8: traversal distances on the low-precision
-// copy; with `rerank` the L pool entries are then measured again on the FP32
-// rows and the k smallest of those keys are returned.
+// form).  P = PREC_BF16 / PREC_FP8 / PREC_U8: traversal distances on the
+// low-precision copy; with `rerank` the L pool entries are then measured again
+// on the FP32 rows and the k smallest of those keys are returned.  The re-rank
+// list reuses the visited hash (no longer needed once the pool is final) when
+// it has room for k keys, else a list of its own (C = k).
 template <int G, int V, int U, int P, bool STOP>
 __device__ __forceinline__ void search_body(const SearchArgs &a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -107,9 +123,22 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
         sc.trace_cap = a.trace_cap;
         const StopCtx *scp = STOP ? &sc : nullptr;
         SearchOut o;
+        bool rerank = a.rerank == 1;
         if constexpr (P == PREC_F32) {
             DistF32<G, V, U> dist{{}, a.base4, a.dp4};
             dist.Q.load(qp, a.d, a.dp4);
+            o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, Lq, s,
+                                                              (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
+                                                              csize, nullptr, 0, scp);
+        } else if constexpr (P == PREC_U8) {
+            // an 8-bit row is a quarter of the FP32 row: G8 lanes of up to
+            // NSG_U8CHUNKS 16-byte chunks each, 32 / G8 rows per pass
+            constexpr int VG = V * G;  // FP32 float4 capacity of a lane group
+            constexpr int G8 = VG / (4 * NSG_U8CHUNKS) < 1 ? 1 : (VG / (4 * NSG_U8CHUNKS) > 32 ? 32 : VG / (4 * NSG_U8CHUNKS));
+            constexpr int VC = VG / (4 * G8);
+            DistU8<G8, VC, NSG_U8ROWS> dist{{}, a.lowp, a.dc};
+            const bool qexact = dist.Q.load(qp, a.d, a.lo, a.scale);
+            rerank = rerank || (a.rerank == 2 && !qexact);
             o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, Lq, s,
                                                               (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
                                                               csize, nullptr, 0, scp);
@@ -125,7 +154,8 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
         }
         const uint64_t *res = s.pool;
         int rsize = o.size;
-        if (P != PREC_F32 && a.rerank) {
+        if (P != PREC_F32 && rerank) {
+            uint64_t *cl = a.C > 0 ? s.clist : reinterpret_cast<uint64_t *>(s.hash);
             DistF32<G, V, U> exact{{}, a.base4, a.dp4};
             exact.Q.load(qp, a.d, a.dp4);
             int kept = 0;
@@ -134,9 +164,9 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
                 for (int t = lane; t < mm; t += 32) s.ids[t] = kid(s.pool[c0 + t]);
                 __syncwarp();
                 exact(s.ids, mm, s.keys);
-                warp_merge(s.clist, kq, kept, s.keys, mm, s.ck, s.cp, s.sk, s.sp);
+                warp_merge(cl, kq, kept, s.keys, mm, s.ck, s.cp, s.sk, s.sp);
             }
-            res = s.clist;
+            res = cl;
             rsize = kept;
         }
         for (int c = lane; c < a.k; c += 32) {  // row stride a.k; slots past this query's k padded
@@ -155,11 +185,16 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
     }
 }
 
-// The fixed-L kernels keep the compiler's default register budget (64 on the
-// common shapes, which lets ~32 warps share an SM); the learned-stop / trace
-// kernels carry the feature and MLP code and are held to 3 blocks per SM.
+// The plain fixed-L kernel keeps the compiler's default register budget (64 on
+// the common shapes, which lets ~32 warps share an SM); the low-precision
+// fixed-L kernels are held to NSG_LOWP_MINB blocks per SM, and the learned-stop
+// / trace kernels, which carry the feature and MLP code, to 3.
 template <int G, int V, int U, int P>
 __global__ void NSG_SEARCH_BOUNDS search_kernel(SearchArgs a) {
+    search_body<G, V, U, P, false>(a);
+}
+template <int G, int V, int U, int P>
+__global__ void __launch_bounds__(256, NSG_LOWP_MINB) search_lp_kernel(SearchArgs a) {
     search_body<G, V, U, P, false>(a);
 }
 template <int G, int V, int U, int P>
@@ -270,8 +305,10 @@ cudaError_t launch_search(const SearchLaunch &l, cudaStream_t st) {
     a.lowp = reinterpret_cast<const uint4 *>(l.lowp);
     a.dc = l.lowp_chunks;
     a.scale = l.lowp_scale;
-    a.rerank = l.precision != PREC_F32 && l.rerank;
-    a.C = a.rerank ? a.k : 0;
+    a.lo = l.lowp_lo;
+    a.rerank = l.precision != PREC_F32 ? l.rerank : 0;
+    // the re-rank list lives in the hash region when k keys fit there
+    a.C = a.rerank && (size_t)a.H * 4 < (size_t)a.k * 8 ? a.k : 0;
     a.stop_model = reinterpret_cast<const __half *>(l.stop_model);
     a.stop_logit = l.stop_logit;
     a.stop_k = l.stop_k;
@@ -289,9 +326,11 @@ cudaError_t launch_search(const SearchLaunch &l, cudaStream_t st) {
     NSG_DISPATCH_DP4(a.dp4, {
         const bool stop = l.stop_model != nullptr || l.trace_feat != nullptr;
         auto kern = l.precision == PREC_BF16
-                        ? (stop ? search_stop_kernel<G_, V_, U_, PREC_BF16> : search_kernel<G_, V_, U_, PREC_BF16>)
+                        ? (stop ? search_stop_kernel<G_, V_, U_, PREC_BF16> : search_lp_kernel<G_, V_, U_, PREC_BF16>)
                     : l.precision == PREC_FP8
-                        ? (stop ? search_stop_kernel<G_, V_, U_, PREC_FP8> : search_kernel<G_, V_, U_, PREC_FP8>)
+                        ? (stop ? search_stop_kernel<G_, V_, U_, PREC_FP8> : search_lp_kernel<G_, V_, U_, PREC_FP8>)
+                    : l.precision == PREC_U8
+                        ? (stop ? search_stop_kernel<G_, V_, U_, PREC_U8> : search_lp_kernel<G_, V_, U_, PREC_U8>)
                         : (stop ? search_stop_kernel<G_, V_, U_, PREC_F32> : search_kernel<G_, V_, U_, PREC_F32>);
         int grid, wpb;
         size_t smem;

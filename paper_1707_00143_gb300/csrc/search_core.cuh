@@ -21,6 +21,13 @@
 
 #include "common.cuh"
 
+// L2 prefetch of an expansion's candidate rows before their gather (1 = on):
+// the FP32 gather takes several rounds of 8 rows, and the later rounds then
+// hit L2.  The 8-bit and BF16 functors gather one or two rounds and skip it.
+#ifndef NSG_PF_ROWS
+#define NSG_PF_ROWS 1
+#endif
+
 namespace nsg {
 
 struct WarpSmem {
@@ -138,6 +145,10 @@ struct DistF32 {
     __device__ __forceinline__ void operator()(const int *ids, int m, uint64_t *keys) const {
         rows_dist<G, V, U>(Q, base4, dp4, ids, m, keys);
     }
+    // rounds of the gather beyond the first exist when m > U * 32 / G
+    __device__ __forceinline__ void prefetch(const int *ids, int m) const {
+        if (m > U * (32 / G)) prefetch_rows_l2(base4, dp4 * 16, ids, m);
+    }
 };
 
 // `dist(ids, m, keys)` writes keys[c] = (d2(query, row ids[c]), ids[c]) for c < m.
@@ -145,7 +156,7 @@ struct DistF32 {
 template <bool COLLECT, bool COHERENT, class D, bool STOP = false>
 __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, WarpSmem &s, uint32_t hmask,
                                int hshift, int max_steps, int excl, int C, int &csize, int *xlog = nullptr,
-                               int xcap = 0, const StopCtx *stop = nullptr) {
+                               int xcap = 0, const StopCtx *stop = nullptr, uint64_t *xthr = nullptr) {
     const unsigned lane = lane_id();
     SearchOut o;
     o.size = 0;
@@ -215,7 +226,12 @@ __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, Warp
         __syncwarp();
         if (lane == 0) s.pool[i] = e | CHK;
         const int u = kid(e);
-        if (xlog != nullptr && lane == 0 && o.n_expand <= xcap) xlog[o.n_expand - 1] = u;  // expanded ids
+        if (xlog != nullptr && lane == 0 && o.n_expand <= xcap) {
+            xlog[o.n_expand - 1] = u;  // expanded ids
+            // and the pool's entry bar at this expansion: a candidate enters
+            // only below the L-th key (anything, while the pool is not full)
+            if (xthr != nullptr) xthr[o.n_expand - 1] = o.size < L ? KEY_INF : kval(s.pool[L - 1]);
+        }
         const int *row = g.adj + (int64_t)u * g.width;
         int m = 0;
         for (int b = 0; b < g.width; b += 32) {
@@ -228,6 +244,9 @@ __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, Warp
         }
         __syncwarp();
         last_m = m;
+#if NSG_PF_ROWS
+        if (m > 0) dist.prefetch(s.ids, m);
+#endif
         if (m == 0) {
             cursor = i + 1;
             if constexpr (STOP) {  // nothing new: the first k entries are unchanged

@@ -123,3 +123,35 @@ def test_knn_deep_shaped_unit_norm(nsg):
     rid, rd2 = oracle.knn_rows(base, 64)
     assert np.allclose(H(d2), rd2, rtol=1e-5, atol=1e-7)
     assert oracle.recall(H(ids), rid, 64) >= 0.999
+
+
+@pytest.fixture
+def small_chunks():
+    # the tensor-core kNN takes the base in chunks (one launch each) and
+    # carries every row's list across them; 3-tile chunks exercise that here
+    os.environ["NSG_KNN_CHUNK_TILES"] = "3"
+    yield
+    os.environ.pop("NSG_KNN_CHUNK_TILES", None)
+
+
+@pytest.mark.parametrize("n,d,k,hi", [(1000, 32, 10, 256), (1300, 128, 100, 3), (700, 128, 256, 256)])
+def test_knn_chunked_base_bit_exact(nsg, small_chunks, n, d, k, hi):
+    base = datagen.uniform_int(n, d, seed=n + 7 * d, hi=hi)
+    ids, d2 = nsg.nsg_knn_init(T(base), k)
+    rid, rd2 = oracle.knn_rows(base, k)
+    assert np.array_equal(H(d2), rd2) and np.array_equal(H(ids), rid)
+    q = datagen.uniform_int(150, d, seed=n + 1, hi=hi)
+    ids, d2 = nsg.nsg_knn_query(T(base), T(q), k)
+    rid, rd2 = oracle.knn_query(base, q, k)
+    assert np.array_equal(H(d2), rd2) and np.array_equal(H(ids), rid)
+
+
+def test_knn_chunked_float_rerank(nsg, small_chunks):
+    base = datagen.uniform_float(1500, 200, seed=67)
+    ids, d2 = nsg.nsg_knn_init(T(base), 20)
+    rid, rd2 = oracle.knn_rows(base, 20)
+    ids, d2 = H(ids), H(d2)
+    assert np.allclose(d2, rd2, rtol=1e-5, atol=0)
+    exact = ((base[ids].astype(np.float64) - base[:, None, :]) ** 2).sum(-1)
+    assert (exact <= rd2[:, -1:].astype(np.float64) * (1 + 1e-5)).all()
+    assert oracle.recall(ids, rid, 20) >= 0.995

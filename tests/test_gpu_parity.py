@@ -135,6 +135,28 @@ def test_search_bit_exact(nsg, tiny, k, L):
     assert (H(out["status"]) == 0).all()
 
 
+@pytest.mark.parametrize("hash_slots", [64, 16384])
+def test_search_rows_listing_an_id_twice(nsg, tiny, hash_slots):
+    # a caller's graph may list a neighbour twice in one row: Alg. 1 visits it
+    # once (S is a set), so results equal the oracle's on the same rows; with
+    # 64 slots the visited set is saturated and forgets, and the pool merge
+    # drops the second copy when both lanes offer it
+    base, q, ref = tiny["base"], tiny["q"], tiny["ref"]
+    adj, deg = ref["adj"].copy(), ref["deg"].copy()
+    rows = np.nonzero(deg < adj.shape[1])[0][::3]
+    adj[rows, deg[rows]] = adj[rows, 0]
+    deg[rows] += 1
+    idx = nsg.nsg_index_from_graph(T(base), T(adj), ref["nav"], deg=T(deg))
+    out = idx.search_ex(T(q), 10, 60, params=nsg.SearchParams(0, hash_slots, nsg.PREC_F32, 0))
+    rid, rd2, rne, rnd = oracle.search(adj, base, ref["nav"], q, 10, 60, deg=deg)
+    assert len(rows) > 100
+    assert np.array_equal(H(out["ids"]), rid)
+    assert np.array_equal(H(out["d2"]), rd2)
+    assert np.array_equal(H(out["n_expand"]), rne)
+    if hash_slots == 16384:
+        assert np.array_equal(H(out["n_dist"]), rnd)
+
+
 @pytest.mark.parametrize("nq", [1, 31, 33, 100])
 def test_search_default_params_and_ragged_batches(nsg, tiny, nq):
     # default (smaller, forgetful) visited set: ids / distances / steps unchanged
