@@ -253,13 +253,20 @@ def main():
             forms[f"{base_name}+stop{th}"] = capi.SearchParams(0, 0, b.precision, 0, -1, stop_model, th, 10)
     info = idx.info()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    out = None
+    outs = {}  # output buffers per result size
+
+    def kq(L):  # results per query at pool size L (k <= L; recall@10 needs 10)
+        return min(K_RESULTS, L)
+
+    def run(L, params):
+        o = idx.search_ex(qt, kq(L), L, params=params, out=outs.get(kq(L)), counters=False)
+        outs[kq(L)] = o
+        return o
 
     def timed(params, L, reps):
-        nonlocal out
         ev0.record(st)
         for _ in range(reps):
-            out = idx.search_ex(qt, K_RESULTS, L, params=params, out=out, counters=False)
+            run(L, params)
         ev1.record(st)
         ev1.synchronize()
         return ev0.elapsed_time(ev1) / reps
@@ -272,8 +279,7 @@ def main():
     for name, prm in forms.items():
         pts = []
         for L in L_GRID:
-            out = idx.search_ex(qt, K_RESULTS, L, params=prm, out=out, counters=False)
-            rec = recall10(out)
+            rec = recall10(run(L, prm))
             ms = timed(prm, L, 2)
             pts.append({"L": L, "recall10": rec, "qps": nq / (ms / 1e3)})
         sweeps[name] = pts
@@ -302,7 +308,8 @@ def main():
 
     # algorithmic bytes at the chosen point: unique distance and expansion counts
     big = capi.SearchParams(0, 16384, prm.precision, 0, prm.rerank)
-    cnt = idx.search_ex(qt, K_RESULTS, L, params=big)
+    kc = kq(L)
+    cnt = idx.search_ex(qt, kc, L, params=big)
     n_dist = cnt["n_dist"].to(torch.int64).sum().item()
     n_expand = cnt["n_expand"].to(torch.int64).sum().item()
     R = info["R"]
@@ -311,12 +318,12 @@ def main():
                  "u8": ((d + 15) // 16) * 16}[base_form]
     lossy = {"plain": False, "bf16": info["has_bf16"] == 1, "fp8": info["has_fp8"] == 1,
              "u8": info["has_u8"] == 1}[base_form]
-    bytes_launch = (n_dist * row_bytes + n_expand * R * 4 + nq * (d * 4 + K_RESULTS * 8)
+    bytes_launch = (n_dist * row_bytes + n_expand * R * 4 + nq * (d * 4 + kc * 8)
                     + (nq * L * d * 4 if lossy else 0))
 
     # timed region: inputs resident in HBM, one search launch per step
     for _ in range(args.warmup):
-        idx.search_ex(qt, K_RESULTS, L, params=prm, out=out, counters=False)
+        run(L, prm)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -326,12 +333,12 @@ def main():
     ms_step = timed(prm, L, args.steps)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    rec_chosen = recall10(out)
+    rec_chosen = recall10(outs[kc])
     # tie-aware recall@10: a returned id counts when its distance is within the
     # true 10th distance (integer data has many exact ties)
-    rec_chosen_ties = (out["d2"][:, :10] <= gt_d2[:, 9:10]).sum().item() / (10.0 * nq)
+    rec_chosen_ties = (outs[kc]["d2"][:, :10] <= gt_d2[:, 9:10]).sum().item() / (10.0 * nq)
     ms_plain = timed(forms["plain"], plain_L, args.steps)
-    rec_plain = recall10(out)
+    rec_plain = recall10(outs[kq(plain_L)])
     if world > 1:
         t = torch.tensor([ms_step, ms_plain], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -340,14 +347,14 @@ def main():
 
     # end to end through the public API with pinned host buffers
     qh = torch.from_numpy(q).pin_memory()
-    ids_h = torch.empty((nq, K_RESULTS), dtype=torch.int32).pin_memory()
+    ids_h = torch.empty((nq, kc), dtype=torch.int32).pin_memory()
     qd = torch.empty_like(qt)
     for i in range(args.warmup + args.steps):
         if i == args.warmup:
             torch.cuda.synchronize()
             e2e_t0 = time.perf_counter()
         qd.copy_(qh, non_blocking=True)
-        o = idx.search_ex(qd, K_RESULTS, L, params=prm, out=out, counters=False)
+        o = idx.search_ex(qd, kc, L, params=prm, out=outs[kc], counters=False)
         ids_h.copy_(o["ids"], non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_ms = 1e3 * (time.perf_counter() - e2e_t0) / args.steps
@@ -399,7 +406,7 @@ def main():
             "dtype": {"plain": "f32", "bf16": "bf16->f32", "fp8": "fp8e4m3->f32", "u8": "u8->i32"}[base_form],
             "data": "synthetic",
             "config": {"workload": W["desc"],
-                       "form": chosen_form, "build": BUILD, "k": K_RESULTS, "L": L,
+                       "form": chosen_form, "build": BUILD, "k": kc, "L": L,
                        "recall10": rec_chosen, "recall10_ties": rec_chosen_ties, "target_recall10": TARGET,
                        "parallelism": f"replicas{world}",
                        "l2": f"inputs larger than L2 ({base.nbytes >> 20} MB base)"},
@@ -409,7 +416,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": world * nq / (e2e_ms / 1e3), "unit": UNIT,
-                    "h2d_bytes_per_step": nq * d * 4, "d2h_bytes_per_step": nq * K_RESULTS * 4},
+                    "h2d_bytes_per_step": nq * d * 4, "d2h_bytes_per_step": nq * kc * 4},
             "gpu_launches": args.steps,
             "clocks": clocks,
             "build_seconds": build_s,

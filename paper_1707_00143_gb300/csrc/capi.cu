@@ -88,10 +88,13 @@ inline unsigned next_pow2(unsigned x) {
 // distances, never changing results) but lets many more warps share an SM;
 // on the 1M x 128 workload 1024 slots beat 8192 by 3.3x (4.8k vs 3.6k
 // distances per query, 24 vs 4 resident warps per SM).
+// Visited-set slots per query.  Small on purpose: the set may forget (results
+// do not change), and 2 KB per warp keeps 28 warps resident per SM; measured
+// on the 1M x 128 workload, 512 slots beat 1024 and 2048 at L = 100..200.
 inline int default_hash(int L, int width) {
     (void)L;
     (void)width;
-    return 1024;
+    return 512;
 }
 inline int default_steps(int L) { return 16 * L + 4096; }
 inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }

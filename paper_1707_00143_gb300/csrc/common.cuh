@@ -134,7 +134,8 @@ __device__ __forceinline__ void prefetch_rows_l2(const void *base, int row_bytes
 // by the pool tail), so results do not change -- only the distance count grows.
 //
 // NSG_HASH_WAYS = 4 (default): slots/4 buckets of 4 ids (one 16-byte word),
-// probed in order from the home bucket, at most HASH_BUCKET_PROBES buckets;
+// probed in order from the home bucket, at most HASH_BUCKET_PROBES buckets
+// (default 1: measured fastest, the recomputations cost less than the probes);
 // a lookup is one 16-byte shared load per bucket.  An id is claimed into the
 // first empty slot of the first bucket that has one (compare-and-swap, so
 // lanes of one warp inserting into one bucket at once all keep their ids);
@@ -151,7 +152,10 @@ __device__ __forceinline__ void prefetch_rows_l2(const void *base, int row_bytes
 #define NSG_HASH_WAYS 4
 #endif
 constexpr int HASH_PROBES = 8;
-constexpr int HASH_BUCKET_PROBES = 4;
+#ifndef NSG_HASH_BUCKET_PROBES
+#define NSG_HASH_BUCKET_PROBES 1
+#endif
+constexpr int HASH_BUCKET_PROBES = NSG_HASH_BUCKET_PROBES;
 
 __device__ __forceinline__ uint4 lds_volatile_u4(const uint4 *p) {
     uint4 v;

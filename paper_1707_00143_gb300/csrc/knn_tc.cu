@@ -38,8 +38,8 @@ namespace {
 constexpr int TC_M = 128;       // query rows per CTA (TMEM lanes)
 constexpr int TC_N = 128;       // base rows per tile (accumulator columns)
 constexpr int TC_BOXK = 64;     // bf16 elements per 128-byte swizzle atom
-constexpr int TC_BUF = 32;      // candidate buffer per row
-constexpr int TC_MERGE_AT = 16; // merge when a buffer holds this many
+constexpr int TC_BUF = 64;      // candidate buffer per row
+constexpr int TC_MERGE_AT = 48; // merge when a buffer holds this many (+ 16 per test < 64)
 constexpr int TC_THREADS = 192;
 constexpr int TC_MAXK = 256;
 
@@ -66,29 +66,37 @@ struct TcCfg {
     static constexpr int KB = DK / TC_BOXK;                     // swizzle atoms along K (resident form)
     static constexpr int A_BYTES = TC_M * DK * 2;
     static constexpr int B_BYTES = DK ? TC_N * DK * 2 : 2 * TC_N * 128;  // one pipeline stage
-    static constexpr int NS = DK == 64 ? 8 : (DK == 128 ? 4 : 5);       // stages
+    static constexpr int NS = DK == 64 ? 8 : (DK == 128 ? 3 : 4);       // stages
     static constexpr int OFF_B = A_BYTES;
     static constexpr int OFF_BUF = OFF_B + NS * B_BYTES;
     static constexpr int OFF_WARP = OFF_BUF + TC_M * TC_BUF * 8;
-    static constexpr int WARP_BYTES = TC_MAXK * 8 + 32 * 8 + TC_N * 4 + 16;
+    static constexpr int WARP_BYTES = TC_MAXK * 8 + TC_BUF * 8 + TC_N * 4 + 16;
     static constexpr int OFF_BAR = OFF_WARP + 4 * WARP_BYTES;
     static constexpr int NBAR = 2 * NS + 6;  // a_full, b_full[NS], b_empty[NS], acc_full[2], acc_empty[2], drain
     static constexpr int SMEM = OFF_BAR + NBAR * 8 + 16 + 1024;  // + alignment slack
 };
 
-__device__ __forceinline__ uint64_t bitonic32(uint64_t v, unsigned lane) {
+// Bitonic sort of 64 keys held two per lane (index lane and lane + 32), ascending.
+__device__ __forceinline__ void bitonic64(uint64_t &a, uint64_t &b, unsigned lane) {
 #pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
+    for (int k = 2; k <= 64; k <<= 1) {
 #pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
-            uint64_t o = __shfl_xor_sync(NSG_FULL, v, j);
-            bool up = (lane & k) == 0;
-            bool lower = (lane & j) == 0;
-            uint64_t mn = o < v ? o : v, mx = o < v ? v : o;
-            v = (lower == up) ? mn : mx;
+            if (j == 32) {  // partner in the same lane: index lane vs lane + 32 (k = 64: ascending)
+                const uint64_t mn = a < b ? a : b, mx = a < b ? b : a;
+                a = mn;
+                b = mx;
+            } else {
+                const uint64_t oa = __shfl_xor_sync(NSG_FULL, a, j), ob = __shfl_xor_sync(NSG_FULL, b, j);
+                const bool lower = (lane & j) == 0;
+                const bool up_a = (lane & k) == 0, up_b = ((lane + 32) & k) == 0;
+                const uint64_t mna = oa < a ? oa : a, mxa = oa < a ? a : oa;
+                const uint64_t mnb = ob < b ? ob : b, mxb = ob < b ? b : ob;
+                a = (lower == up_a) ? mna : mxa;
+                b = (lower == up_b) ? mnb : mxb;
+            }
         }
     }
-    return v;
 }
 
 __device__ __forceinline__ int count_less(const uint64_t *a, int len, uint64_t key) {
@@ -101,7 +109,10 @@ __device__ __forceinline__ int count_less(const uint64_t *a, int len, uint64_t k
     return lo;
 }
 
-// Merge row `src`'s buffer into its sorted list (warp-cooperative).
+// Merge row `src`'s buffer (c <= 63 keys) into its sorted list of s keys
+// (output arrays, capacity KL), warp-cooperatively: the list is read once
+// (all loads issued before use), the buffer sorted, and every key written to
+// its rank in the union.
 __device__ __noinline__ void merge_row(int src, int row_local, int64_t row_g, int &cnt, int &lsize,
                                        float &thrp, float qn_r, const uint64_t *bufs, uint64_t *ls,
                                        uint64_t *sb, uint64_t *thr_slot, int *ids, float *d2, int KL) {
@@ -112,26 +123,51 @@ __device__ __noinline__ void merge_row(int src, int row_local, int64_t row_g, in
     const int64_t rg = __shfl_sync(NSG_FULL, row_g, src);
     int *oid = ids + rg * KL;
     float *od = d2 + rg * KL;
-    for (int i = lane; i < s; i += 32) ls[i] = make_key(od[i], oid[i]);
-    uint64_t b = (int)lane < c ? bufs[rl * TC_BUF + lane] : ~0ull;
-    b = bitonic32(b, lane);
-    sb[lane] = b;
-    __syncwarp();
-    for (int i = lane; i < s; i += 32) {
-        const uint64_t key = ls[i];
-        const int p = i + count_less(sb, c, key);
-        if (p < KL) {
-            od[p] = kd2(key);
-            oid[p] = kid(key);
-            if (p == KL - 1) *thr_slot = key;
+    float lv[TC_MAXK / 32];
+    int li[TC_MAXK / 32];
+#pragma unroll
+    for (int t = 0; t < TC_MAXK / 32; ++t) {
+        const int i = t * 32 + (int)lane;
+        if (i < s) {
+            lv[t] = od[i];
+            li[t] = oid[i];
         }
     }
-    if ((int)lane < c) {
-        const int p = lane + count_less(ls, s, b);
-        if (p < KL) {
-            od[p] = kd2(b);
-            oid[p] = kid(b);
-            if (p == KL - 1) *thr_slot = b;
+    uint64_t a = (int)lane < c ? bufs[rl * TC_BUF + lane] : ~0ull;
+    uint64_t b = (int)lane + 32 < c ? bufs[rl * TC_BUF + 32 + lane] : ~0ull;
+    bitonic64(a, b, lane);
+    sb[lane] = a;
+    sb[lane + 32] = b;
+#pragma unroll
+    for (int t = 0; t < TC_MAXK / 32; ++t) {
+        const int i = t * 32 + (int)lane;
+        if (i < s) ls[i] = make_key(lv[t], li[t]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < TC_MAXK / 32; ++t) {
+        const int i = t * 32 + (int)lane;
+        if (i < s) {
+            const uint64_t key = ls[i];
+            const int p = i + count_less(sb, c, key);
+            if (p < KL) {
+                od[p] = kd2(key);
+                oid[p] = kid(key);
+                if (p == KL - 1) *thr_slot = key;
+            }
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int j = (int)lane + 32 * h;
+        const uint64_t key = h ? b : a;
+        if (j < c) {
+            const int p = j + count_less(ls, s, key);
+            if (p < KL) {
+                od[p] = kd2(key);
+                oid[p] = kid(key);
+                if (p == KL - 1) *thr_slot = key;
+            }
         }
     }
     __syncwarp();
@@ -283,7 +319,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         unsigned char *wsm = smem + Cfg::OFF_WARP + ew * Cfg::WARP_BYTES;
         uint64_t *ls = reinterpret_cast<uint64_t *>(wsm);
         uint64_t *sb = ls + TC_MAXK;
-        float *xs = reinterpret_cast<float *>(sb + 32);
+        float *xs = reinterpret_cast<float *>(sb + TC_BUF);
         uint64_t *thr_slot = reinterpret_cast<uint64_t *>(xs + TC_N);
         const int row_local = q * 32 + lane;
         const int64_t row_g = row0 + row_local;
@@ -349,11 +385,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (int j = 0; j < 4; ++j) m8[j] = fminf(m8[2 * j], m8[2 * j + 1]);
                     const float mn = fminf(fminf(m8[0], m8[1]), fminf(m8[2], m8[3]));
                     if (mn < thrp) {
+                        // columns of this group that exist and are not the row itself
+                        const int nv = lim - jb;
+                        unsigned vm = nv >= 16 ? 0xffffu : (nv <= 0 ? 0u : (1u << nv) - 1u);
+                        if ((unsigned)(self_local - jb) < 16u) vm &= ~(1u << (self_local - jb));
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            const int jj = jb + j;
-                            if (tv[j] < thrp && jj < lim && jj != self_local) {
-                                mybuf[cnt] = make_key(fmaxf(qn_r + tv[j], 0.0f), (int)(col0 + jj));
+                            if (tv[j] < thrp && ((vm >> j) & 1u)) {
+                                mybuf[cnt] = make_key(fmaxf(qn_r + tv[j], 0.0f), (int)(col0 + jb + j));
                                 ++cnt;
                             }
                         }

@@ -29,7 +29,7 @@
 #define NSG_UL2 2
 #endif
 #ifndef NSG_U8ROWS
-#define NSG_U8ROWS 2
+#define NSG_U8ROWS 3
 #endif
 #ifndef NSG_U8CHUNKS
 #define NSG_U8CHUNKS 2
