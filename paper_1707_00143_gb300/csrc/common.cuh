@@ -7,6 +7,8 @@
 // pool and is masked out of every comparison.
 #pragma once
 
+#include <climits>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -289,6 +291,7 @@ __device__ __forceinline__ int warp_merge(uint64_t *list, int cap, int &size, co
         // one node offered twice in this batch (a row that lists an id twice):
         // equal keys sit next to each other in sk; keep the first of each run
         int w = 0;
+        uint64_t before = ~0ull;  // original key just below this chunk
         for (int b = 0; b < nk; b += 32) {
             const int j = b + (int)lane;
             uint64_t k = 0;
@@ -297,8 +300,10 @@ __device__ __forceinline__ int warp_merge(uint64_t *list, int cap, int &size, co
             if (j < nk) {
                 k = sk[j];
                 p = sp[j];
-                keep = j == 0 || sk[j - 1] != k;
+                const uint64_t prev = lane == 0 ? before : sk[j - 1];
+                keep = j == 0 || prev != k;
             }
+            before = __shfl_sync(NSG_FULL, k, 31);
             const unsigned bal = __ballot_sync(NSG_FULL, keep);
             __syncwarp();
             if (keep) {
@@ -312,18 +317,23 @@ __device__ __forceinline__ int warp_merge(uint64_t *list, int cap, int &size, co
         nk = w;
     }
     const int lo = sp[0];
-    // move old entries i >= lo to i + #{r : sp[r] <= i}, top chunk first
+    // move old entries i >= lo to i + #{r : sp[r] <= i}, top chunk first.  An
+    // entry only moves up, so a chunk's writes land in chunks already read:
+    // one barrier per chunk (between its reads and its writes) suffices.  Up
+    // to 4 kept candidates (the common case) the count is 4 compares.
+    const bool few = nk <= 4;
+    const int p0 = sp[0], p1 = nk > 1 ? sp[1] : INT_MAX, p2 = nk > 2 ? sp[2] : INT_MAX,
+              p3 = nk > 3 ? sp[3] : INT_MAX;
     for (int c = ((size - 1) >> 5) << 5; c >= (lo & ~31); c -= 32) {
         int i = c + (int)lane;
         uint64_t e = 0;
         int dst = cap;
         if (i >= lo && i < size) {
             e = list[i];
-            dst = i + count_le(sp, nk, i);
+            dst = i + (few ? (p0 <= i) + (p1 <= i) + (p2 <= i) + (p3 <= i) : count_le(sp, nk, i));
         }
         __syncwarp();
         if (dst < cap) list[dst] = e;
-        __syncwarp();
     }
     for (int r = lane; r < nk; r += 32) {
         int f = sp[r] + r;

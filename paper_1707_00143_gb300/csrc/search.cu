@@ -8,20 +8,9 @@
 #include "lowp.cuh"
 #include "search_core.cuh"
 
-// Launch shape of the search kernels: minimum resident 256-thread blocks per
-// SM (bounds the registers per thread) of the plain and the low-precision
-// kernels, and rows in flight per lane group on the low-precision paths (1 or
-// 2 16-byte chunks per lane; NSG_U8ROWS for the 8-bit form).  Left unbounded
-// the low-precision kernels, which also carry the FP32 re-rank, take ~112
-// registers and half the resident warps.
-#ifdef NSG_SEARCH_MINB
-#define NSG_SEARCH_BOUNDS __launch_bounds__(256, NSG_SEARCH_MINB)
-#else
-#define NSG_SEARCH_BOUNDS __launch_bounds__(256)
-#endif
-#ifndef NSG_LOWP_MINB
-#define NSG_LOWP_MINB 4
-#endif
+// Rows in flight per lane group on the low-precision paths (1 or 2 16-byte
+// chunks per lane; NSG_U8ROWS row groups of NSG_U8CHUNKS chunks per lane for
+// the 8-bit form).
 #ifndef NSG_UL1
 #define NSG_UL1 2
 #endif
@@ -185,21 +174,32 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
     }
 }
 
-// The plain fixed-L kernel keeps the compiler's default register budget (64 on
-// the common shapes, which lets ~32 warps share an SM); the low-precision
-// fixed-L kernels are held to NSG_LOWP_MINB blocks per SM, and the learned-stop
-// / trace kernels, which carry the feature and MLP code, to 3.
+// Register budgets.  Rows of up to 512 values (V <= 4 float4 slices per lane)
+// are held to 4 blocks of 256 threads per SM, i.e. 64 registers and 32
+// resident warps, with no spills; left free, the low-precision kernels (which
+// also carry the FP32 re-rank) take ~112 registers and the plain one 70.
+// Wider rows (V >= 8) keep the compiler's default budget (~98), since 64 would
+// spill.  The learned-stop / trace kernels carry the feature and MLP code and
+// are held to 3 blocks per SM.
 template <int G, int V, int U, int P>
-__global__ void NSG_SEARCH_BOUNDS search_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a) {
     search_body<G, V, U, P, false>(a);
 }
 template <int G, int V, int U, int P>
-__global__ void __launch_bounds__(256, NSG_LOWP_MINB) search_lp_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(256) search_wide_kernel(SearchArgs a) {
     search_body<G, V, U, P, false>(a);
 }
 template <int G, int V, int U, int P>
 __global__ void __launch_bounds__(256, 3) search_stop_kernel(SearchArgs a) {
     search_body<G, V, U, P, true>(a);
+}
+
+// Kernel for precision P at the dispatch shape G, V, U.
+template <int G, int V, int U, int P>
+static void (*search_entry(bool stop))(SearchArgs) {
+    if (stop) return search_stop_kernel<G, V, U, P>;
+    if constexpr (V <= 4) return search_kernel<G, V, U, P>;
+    else return search_wide_kernel<G, V, U, P>;
 }
 
 struct CollectArgs {
@@ -325,13 +325,10 @@ cudaError_t launch_search(const SearchLaunch &l, cudaStream_t st) {
     cudaError_t err = cudaSuccess;
     NSG_DISPATCH_DP4(a.dp4, {
         const bool stop = l.stop_model != nullptr || l.trace_feat != nullptr;
-        auto kern = l.precision == PREC_BF16
-                        ? (stop ? search_stop_kernel<G_, V_, U_, PREC_BF16> : search_lp_kernel<G_, V_, U_, PREC_BF16>)
-                    : l.precision == PREC_FP8
-                        ? (stop ? search_stop_kernel<G_, V_, U_, PREC_FP8> : search_lp_kernel<G_, V_, U_, PREC_FP8>)
-                    : l.precision == PREC_U8
-                        ? (stop ? search_stop_kernel<G_, V_, U_, PREC_U8> : search_lp_kernel<G_, V_, U_, PREC_U8>)
-                        : (stop ? search_stop_kernel<G_, V_, U_, PREC_F32> : search_kernel<G_, V_, U_, PREC_F32>);
+        auto kern = l.precision == PREC_BF16  ? search_entry<G_, V_, U_, PREC_BF16>(stop)
+                    : l.precision == PREC_FP8 ? search_entry<G_, V_, U_, PREC_FP8>(stop)
+                    : l.precision == PREC_U8  ? search_entry<G_, V_, U_, PREC_U8>(stop)
+                                              : search_entry<G_, V_, U_, PREC_F32>(stop);
         int grid, wpb;
         size_t smem;
         err = config(kern, per_warp, l.warps_per_cta, l.nq, &grid, &wpb, &smem, per_cta);

@@ -234,11 +234,28 @@ __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, Warp
         }
         const int *row = g.adj + (int64_t)u * g.width;
         int m = 0;
-        for (int b = 0; b < g.width; b += 32) {
-            int slot = b + (int)lane;
-            int v = slot < g.width ? load_adj<COHERENT>(row + slot) : -1;
-            bool fresh = v >= 0 && visit(s.hash, hmask, hshift, v);
-            unsigned bal = __ballot_sync(NSG_FULL, fresh);
+        // the first 128 slots of the row are loaded before any visit (the
+        // visited-set updates would otherwise order each 32-slot load after
+        // the previous chunk's), so a row costs one global round trip
+        int vr[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int slot = c * 32 + (int)lane;
+            vr[c] = slot < g.width ? load_adj<COHERENT>(row + slot) : -1;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (c * 32 >= g.width) break;
+            const bool fresh = vr[c] >= 0 && visit(s.hash, hmask, hshift, vr[c]);
+            const unsigned bal = __ballot_sync(NSG_FULL, fresh);
+            if (fresh) s.ids[m + __popc(bal & lanemask_lt())] = vr[c];
+            m += __popc(bal);
+        }
+        for (int b = 128; b < g.width; b += 32) {  // rows wider than 128
+            const int slot = b + (int)lane;
+            const int v = slot < g.width ? load_adj<COHERENT>(row + slot) : -1;
+            const bool fresh = v >= 0 && visit(s.hash, hmask, hshift, v);
+            const unsigned bal = __ballot_sync(NSG_FULL, fresh);
             if (fresh) s.ids[m + __popc(bal & lanemask_lt())] = v;
             m += __popc(bal);
         }
