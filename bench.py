@@ -53,11 +53,11 @@ WORKLOADS = {
                  desc="sift-shaped 1,000,000 x 128 int 0..255 GMM(100), 10,000 queries"),
     "gist": dict(build=dict(K=100, L=60, R=70, C=500), L_grid=[10, 20, 40, 60, 80, 100, 150, 200, 300, 400, 500],
                  k=100, desc="gist-shaped 1,000,000 x 960 f32 [0,1] GMM(50), 1,000 queries"),
-    "deep": dict(build=dict(K=64, L=60, R=32, C=500), L_grid=[20, 40, 60, 80, 100, 150, 200, 300, 400, 500],
+    "deep": dict(build=dict(K=64, L=60, R=32, C=500), L_grid=[20, 40, 60, 100, 150, 200, 300, 400, 500, 700, 1000],
                  k=100, desc="deep-shaped 10,000,000 x 96 f32 unit-norm GMM(1000), 100,000 queries"),
 }
-STOP_TRACE_L, STOP_TRACE_CAP, STOP_ITERS = 250, 1024, 300
-STOP_THRESHOLDS = [0.5, 0.7, 0.9]
+STOP_TRACE_LS, STOP_TRACE_CAP, STOP_ITERS = (100, 200, 400), 1024, 300
+STOP_THRESHOLDS = [0.9, 0.95, 0.98]
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -132,7 +132,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("common.cuh", "search_core.cuh", "search.cu"):
+    for f in ("common.cuh", "search_core.cuh", "lowp.cuh", "search.cu"):
         with open(os.path.join(ROOT, "paper_1707_00143_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -242,9 +242,15 @@ def main():
     # seed, never timed) -> MLP trained on the GPU -> stop rule in the kernel
     _, q_train = datagen.workload(args.workload, nq=nq, seed_query=datagen.SEED_QUERY + 500 + 1000 * rank)
     t1 = time.perf_counter()
-    trace = idx.search_trace(torch.from_numpy(q_train).cuda(), 10, STOP_TRACE_L, STOP_TRACE_CAP,
-                             params=capi.SearchParams(0, 0, capi.PREC_F32, 0, -1, None, 0.5, 10))
+    # traces at three pool sizes (the features are relative to L), one model
+    qtr = torch.from_numpy(q_train).cuda()
+    parts = [idx.search_trace(qtr[i::len(STOP_TRACE_LS)].contiguous(), 10, Lt, STOP_TRACE_CAP,
+                              params=capi.SearchParams(0, 0, capi.PREC_F32, 0, -1, None, 0.5, 10))
+             for i, Lt in enumerate(STOP_TRACE_LS)]
+    trace = {key: torch.cat([t[key] for t in parts]) for key in ("feat", "flag", "steps")}
+    del parts
     stop_model, _, stop_loss = capi.nsg_stop_train(trace, iters=STOP_ITERS, lr=1e-2, seed=1)
+    del trace
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
     for th in STOP_THRESHOLDS:
@@ -428,7 +434,7 @@ def main():
                       "fp8_scale": info["fp8_scale"]},
             "per_query": {"n_expand": n_expand / nq, "n_dist": n_dist / nq},
             "batched": batched,
-            "learned_stop": {"train_queries": nq, "trace_L": STOP_TRACE_L, "iters": STOP_ITERS,
+            "learned_stop": {"train_queries": nq, "trace_L": list(STOP_TRACE_LS), "iters": STOP_ITERS,
                              "train_seconds": train_s, "loss_first": stop_loss[0].item(),
                              "loss_last": stop_loss[-1].item(), "thresholds": STOP_THRESHOLDS},
             "precision_error_vs_fp64": prec_err,

@@ -65,11 +65,18 @@ typedef struct {
                                device (see nsg_stop_train), or NULL for the fixed-L search */
     float stop_threshold;  /* stop once the model's probability exceeds this (0..1) */
     int32_t stop_k;        /* result size the stop rule protects (<= 0 -> min(k, 10)) */
-    int32_t stop_min_steps; /* never stop before this many expansions */
+    int32_t stop_min_steps; /* never stop before this many expansions; the rule is
+                               evaluated at min_steps, min_steps + 4, min_steps + 8, ... */
 } nsg_search_params;
 
 /* Parameters of the early-termination MLP (8 features -> 64 ReLU -> 1):
- * w1[64][8], b1[64], w2[64], b2 in this order. */
+ * w1[64][8], b1[64], w2[64], b2 in this order.  The features, formed before
+ * each expansion from the pool S (size |S|, k = stop_k, i = position of the
+ * entry about to be expanded, t = expansions so far):
+ *   0  min(t / L, 4) / 4            4  log2(1 + steps since the first k changed) / 8
+ *   1  d(S[0]) / d(S[k-1])          5  i / L
+ *   2  min(d(S[k-1]) / d(S[i]), 4)  6  new neighbours at the last expansion / R
+ *   3  d(S[k-1]) / d(S[|S|-1])      7  1 if the last expansion changed the first k */
 #define NSG_STOP_FEATURES 8
 #define NSG_STOP_PARAMS 641
 

@@ -94,6 +94,9 @@ struct SearchOut {
 // first k_stop pool entries changed are recorded (the training data).
 // ---------------------------------------------------------------------------
 #define NSG_STOP_NF 8
+#ifndef NSG_STOP_EVERY
+#define NSG_STOP_EVERY 4
+#endif
 #define NSG_STOP_H 64
 #define NSG_STOP_PARAMS (NSG_STOP_H * NSG_STOP_NF + 2 * NSG_STOP_H + 1)  // w1, b1, w2, b2
 
@@ -195,18 +198,22 @@ __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, Warp
             o.capped = true;
             break;
         }
-        if constexpr (STOP) {
+        // the learned stop rule is evaluated after stop_min_steps expansions and
+        // every NSG_STOP_EVERY after that; traces record features at every one
+        if constexpr (STOP) if (stop->trace_feat != nullptr ||
+                                (stop->mlp != nullptr && o.n_expand >= stop->min_steps &&
+                                 (o.n_expand - stop->min_steps) % NSG_STOP_EVERY == 0)) {
             // state before expanding pool[i]: every lane computes the same features
             const int kk = stop->k < o.size ? stop->k : o.size;
             const float d0 = kd2(s.pool[0]), dk = kd2(s.pool[kk - 1]);
             const float dn = kd2(s.pool[i]), dl = kd2(s.pool[o.size - 1]);
             float f[NSG_STOP_NF];
-            f[0] = log2f(1.0f + (float)o.n_expand) * 0.1f;
+            f[0] = fminf((float)o.n_expand / (float)L, 4.0f) * 0.25f;  // progress relative to the pool size
             f[1] = dk > 0.0f ? d0 / dk : 1.0f;
             f[2] = dn > 0.0f ? fminf(dk / dn, 4.0f) : 1.0f;
             f[3] = dl > 0.0f ? dk / dl : 1.0f;
             f[4] = log2f(1.0f + (float)since_change) * 0.125f;
-            f[5] = log2f(1.0f + (float)i) * 0.1f;
+            f[5] = (float)i / (float)L;  // position of the next expansion in the pool
             f[6] = (float)last_m / (float)g.width;
             f[7] = last_changed ? 1.0f : 0.0f;
             if (stop->trace_feat != nullptr && o.n_expand < stop->trace_cap) {

@@ -52,7 +52,8 @@ def test_trace_flags_match_oracle_pool_trace(nsg, setup):
             prev = cur
         f = feat[i, :steps[i]]
         assert np.isfinite(f).all()
-        assert np.allclose(f[:, 0], np.log2(1 + np.arange(steps[i])) * 0.1, atol=1e-6)
+        assert np.allclose(f[:, 0], np.minimum(np.arange(steps[i]) / L, 4.0) * 0.25, atol=1e-6)
+        assert (f[:, 5] >= 0).all() and (f[:, 5] < 1).all()
         assert (f[:, 1] >= 0).all() and (f[:, 1] <= 1).all() and (f[:, 3] <= 1).all()
 
 
