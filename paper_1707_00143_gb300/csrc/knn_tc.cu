@@ -66,11 +66,13 @@ struct TcCfg {
     static constexpr int KB = DK / TC_BOXK;                     // swizzle atoms along K (resident form)
     static constexpr int A_BYTES = TC_M * DK * 2;
     static constexpr int B_BYTES = DK ? TC_N * DK * 2 : 2 * TC_N * 128;  // one pipeline stage
-    static constexpr int NS = DK == 64 ? 8 : (DK == 128 ? 3 : 4);       // stages
+    static constexpr int NS = DK == 64 ? 7 : (DK == 128 ? 3 : 4);       // stages
     static constexpr int OFF_B = A_BYTES;
     static constexpr int OFF_BUF = OFF_B + NS * B_BYTES;
     static constexpr int OFF_WARP = OFF_BUF + TC_M * TC_BUF * 8;
-    static constexpr int WARP_BYTES = TC_MAXK * 8 + TC_BUF * 8 + TC_N * 4 + 16;
+    // per epilogue warp: merge list, sorted buffer, base norms, k-th slot, and
+    // 16 values per lane for the insertion path (column-major, conflict-free)
+    static constexpr int WARP_BYTES = TC_MAXK * 8 + TC_BUF * 8 + TC_N * 4 + 16 + 16 * 32 * 4;
     static constexpr int OFF_BAR = OFF_WARP + 4 * WARP_BYTES;
     static constexpr int NBAR = 2 * NS + 6;  // a_full, b_full[NS], b_empty[NS], acc_full[2], acc_empty[2], drain
     static constexpr int SMEM = OFF_BAR + NBAR * 8 + 16 + 1024;  // + alignment slack
@@ -321,6 +323,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint64_t *sb = ls + TC_MAXK;
         float *xs = reinterpret_cast<float *>(sb + TC_BUF);
         uint64_t *thr_slot = reinterpret_cast<uint64_t *>(xs + TC_N);
+        float *tvs = reinterpret_cast<float *>(thr_slot + 2);  // [16][32]
         const int row_local = q * 32 + lane;
         const int64_t row_g = row0 + row_local;
         const bool valid = row_g < a.m;
@@ -385,14 +388,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (int j = 0; j < 4; ++j) m8[j] = fminf(m8[2 * j], m8[2 * j + 1]);
                     const float mn = fminf(fminf(m8[0], m8[1]), fminf(m8[2], m8[3]));
                     if (mn < thrp) {
-                        // columns of this group that exist and are not the row itself
+                        // columns of this group that exist, are not the row itself, and
+                        // beat the threshold: a bit mask, then one step per set bit
                         const int nv = lim - jb;
                         unsigned vm = nv >= 16 ? 0xffffu : (nv <= 0 ? 0u : (1u << nv) - 1u);
                         if ((unsigned)(self_local - jb) < 16u) vm &= ~(1u << (self_local - jb));
+                        unsigned msk = 0;
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            if (tv[j] < thrp && ((vm >> j) & 1u)) {
-                                mybuf[cnt] = make_key(fmaxf(qn_r + tv[j], 0.0f), (int)(col0 + jb + j));
+                        for (int j = 0; j < 16; ++j) msk |= (tv[j] < thrp ? 1u : 0u) << j;
+                        msk &= vm;
+                        if (msk) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) tvs[j * 32 + lane] = tv[j];
+                            while (msk) {
+                                const int j = __ffs(msk) - 1;
+                                msk &= msk - 1;
+                                mybuf[cnt] = make_key(fmaxf(qn_r + tvs[j * 32 + lane], 0.0f), (int)(col0 + jb + j));
                                 ++cnt;
                             }
                         }

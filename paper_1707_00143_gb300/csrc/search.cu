@@ -11,6 +11,9 @@
 // Rows in flight per lane group on the low-precision paths (1 or 2 16-byte
 // chunks per lane; NSG_U8ROWS row groups of NSG_U8CHUNKS chunks per lane for
 // the 8-bit form).
+#ifndef NSG_STOP_MINB
+#define NSG_STOP_MINB 3
+#endif
 #ifndef NSG_UL1
 #define NSG_UL1 2
 #endif
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(256) search_wide_kernel(SearchArgs a) {
     search_body<G, V, U, P, false>(a);
 }
 template <int G, int V, int U, int P>
-__global__ void __launch_bounds__(256, 3) search_stop_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(256, NSG_STOP_MINB) search_stop_kernel(SearchArgs a) {
     search_body<G, V, U, P, true>(a);
 }
 
