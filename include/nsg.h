@@ -223,6 +223,9 @@ nsg_status nsg_index_from_graph(const float *base_dev, int64_t n, int32_t d, con
  *   i32 out; d2_dev [nq][k] f32 out (nullable).  1 <= k <= L <= 1024.
  *   Returns NSG_ESTEPCAP (after the stream finishes) if any query hit its
  *   cap -- nsg_search synchronises only in that check.
+ *   Warps draw queries from a device counter owned by the index (256 of
+ *   them, used in turn): calls on one stream are ordered; at most 256 calls
+ *   on one index may be in flight on different streams at once.
  * nsg_search_ex: same with parameters and optional per-query outputs
  *   n_expand_dev [nq] (nodes checked), n_dist_dev [nq] (distances computed),
  *   status_dev [nq] (0 or NSG_ESTEPCAP).  Does not synchronise.

@@ -8,11 +8,14 @@
 #include <cstdio>
 #include <cstdlib>
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <vector>
 
 #include "kernels.h"
 #include "nsg.h"
+
+constexpr unsigned kWorkSlots = 256;
 
 struct nsg_index {
     int64_t n = 0;
@@ -21,6 +24,10 @@ struct nsg_index {
     int *adj = nullptr;     // [n][R], -1 padded
     int *deg = nullptr;     // [n]
     int *flag = nullptr;    // [4] device scratch for nsg_search's cap check
+    // work counters of the search launches (warps draw queries from one),
+    // used round-robin so concurrent calls on other streams take other slots
+    int *work = nullptr;    // [kWorkSlots]
+    mutable std::atomic<unsigned> work_next{0};
     // low-precision copies, indexed by nsg_precision (1 = BF16, 2 = FP8-e4m3, 3 = U8)
     void *lowp[4] = {nullptr, nullptr, nullptr, nullptr};  // by nsg_precision
     int lowp_dpl[4] = {0, 0, 0, 0};         // values per row (16-byte multiple)
@@ -84,10 +91,6 @@ inline unsigned next_pow2(unsigned x) {
     while (p < x) p <<= 1;
     return p;
 }
-// Visited-hash slots per warp.  A small table forgets (costing recomputed
-// distances, never changing results) but lets many more warps share an SM;
-// on the 1M x 128 workload 1024 slots beat 8192 by 3.3x (4.8k vs 3.6k
-// distances per query, 24 vs 4 resident warps per SM).
 // Visited-set slots per query.  Small on purpose: the set may forget (results
 // do not change), and 2 KB per warp keeps 28 warps resident per SM; measured
 // on the 1M x 128 workload, 512 slots beat 1024 and 2048 at L = 100..200.
@@ -292,6 +295,7 @@ nsg_status finish_index(nsg_index *ix, cudaStream_t st) {
     ix->max_degree = mx;
     ix->avg_degree = ix->n ? (double)sum / (double)ix->n : 0.0;
     NSG_CK(cudaMalloc(reinterpret_cast<void **>(&ix->flag), 4 * sizeof(int)));
+    NSG_CK(cudaMalloc(reinterpret_cast<void **>(&ix->work), kWorkSlots * sizeof(int)));
     return NSG_OK;
 }
 
@@ -301,6 +305,7 @@ void destroy(nsg_index *ix) {
     if (ix->adj) cudaFree(ix->adj);
     if (ix->deg) cudaFree(ix->deg);
     if (ix->flag) cudaFree(ix->flag);
+    if (ix->work) cudaFree(ix->work);
     for (void *p : ix->lowp)
         if (p) cudaFree(p);
     delete ix;
@@ -666,6 +671,20 @@ nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t n
     return NSG_OK;
 }
 
+// Search launch whose warps draw queries from a device counter: a warp that
+// finishes early takes the next query, instead of a fixed share of
+// ceil(nq / warps) queries leaving a tail of warps on their last one.  The
+// counter is one of the index's kWorkSlots, taken round-robin and zeroed on
+// the launch's stream, so calls on one stream are ordered and up to
+// kWorkSlots calls may run concurrently on different streams.
+nsg_status launch_dynamic(const nsg_index *idx, nsg::SearchLaunch l, cudaStream_t st) {
+    int *ctr = idx->work + (idx->work_next.fetch_add(1, std::memory_order_relaxed) % kWorkSlots);
+    NSG_CK(cudaMemsetAsync(ctr, 0, sizeof(int), st));
+    l.work = ctr;
+    NSG_CK(nsg::launch_search(l, st));
+    return NSG_OK;
+}
+
 }  // namespace
 
 nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k,
@@ -675,8 +694,7 @@ nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t
     nsg_status s = make_search(idx, queries_dev, nq, k, L, params, ids_dev, d2_dev, n_expand_dev, n_dist_dev,
                                status_dev, l);
     if (s || nq == 0) return s;
-    NSG_CK(nsg::launch_search(l, S(stream)));
-    return NSG_OK;
+    return launch_dynamic(idx, l, S(stream));
 }
 
 }  // extern "C"
@@ -956,7 +974,7 @@ nsg_status nsg_search(const nsg_index *idx, const float *queries_dev, int64_t nq
     l.status = nullptr;
     l.any_capped = idx->flag;
     NSG_CK(cudaMemsetAsync(idx->flag, 0, sizeof(int), st));
-    NSG_CK(nsg::launch_search(l, st));
+    if (nsg_status ls = launch_dynamic(idx, l, st)) return ls;
     int h = 0;
     NSG_CK(cudaMemcpyAsync(&h, idx->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     NSG_CK(cudaStreamSynchronize(st));

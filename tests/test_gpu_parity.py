@@ -121,7 +121,7 @@ def test_build_bit_exact(nsg, tiny):
     assert info["max_degree"] <= R
 
 
-@pytest.mark.parametrize("k,L", [(10, 50), (1, 10), (16, 16), (100, 137), (10, 400)])
+@pytest.mark.parametrize("k,L", [(10, 50), (1, 10), (16, 16), (100, 137), (10, 400), (10, 1024)])
 def test_search_bit_exact(nsg, tiny, k, L):
     base, q, ref = tiny["base"], tiny["q"], tiny["ref"]
     idx = nsg.nsg_index_from_graph(T(base), T(ref["adj"]), ref["nav"], deg=T(ref["deg"]))
@@ -245,3 +245,38 @@ def test_small_graph_pads_results(nsg):
     ids, d2 = H(ids), H(d2)
     assert (ids[:, 2:] == -1).all() and np.isinf(d2[:, 2:]).all()
     assert set(ids[0, :2]) == {0, 1}
+
+
+@pytest.mark.parametrize("d,hi", [(600, 64), (1500, 32)])
+def test_wide_rows_search_bit_exact(nsg, d, hi):
+    # rows wider than 512 values take the wide search kernels (8 and 16 float4
+    # slices per lane); integer data small enough that every squared distance
+    # stays below 2^24 keeps FP32 exact, so the results are the oracle's
+    base = datagen.uniform_int(2500, d, seed=d, hi=hi)
+    q = datagen.uniform_int(70, d, seed=d + 1, hi=hi)
+    ref = oracle.build(base, 12, 30, 12, 100, seed=0)
+    idx = nsg.nsg_index_from_graph(T(base), T(ref["adj"]), ref["nav"], deg=T(ref["deg"]))
+    out = idx.search_ex(T(q), 10, 48, params=nsg.SearchParams(0, 16384, nsg.PREC_F32, 0))
+    rid, rd2, rne, rnd = oracle.search(ref["adj"], base, ref["nav"], q, 10, 48, deg=ref["deg"])
+    assert np.array_equal(H(out["ids"]), rid)
+    assert np.array_equal(H(out["d2"]), rd2)
+    assert np.array_equal(H(out["n_expand"]), rne)
+    assert np.array_equal(H(out["n_dist"]), rnd)
+    # and the GPU build of the same rows equals the oracle's graph
+    g = nsg.nsg_build(T(base), 12, 30, 12, 100, seed=0)
+    adj, deg = g.graph()
+    assert g.info()["nav"] == ref["nav"]
+    assert np.array_equal(H(deg), ref["deg"]) and np.array_equal(H(adj), ref["adj"])
+
+
+def test_float_rows_search_within_tolerance(nsg):
+    # float data: distances agree to 1e-5 relative; ids may differ only at
+    # near-ties, so recall against the oracle's ids stays within 0.001
+    base, q = datagen.workload("gist", n=3000, nq=60)
+    ref = oracle.build(base, 16, 40, 24, 150, seed=0)
+    idx = nsg.nsg_index_from_graph(T(base), T(ref["adj"]), ref["nav"], deg=T(ref["deg"]))
+    out = idx.search_ex(T(q), 10, 60, params=nsg.SearchParams(0, 16384, nsg.PREC_F32, 0))
+    rid, rd2, _, _ = oracle.search(ref["adj"], base, ref["nav"], q, 10, 60, deg=ref["deg"])
+    ids, d2 = H(out["ids"]), H(out["d2"])
+    assert np.allclose(d2, rd2, rtol=1e-5, atol=0)
+    assert oracle.recall(ids, rid, 10) >= 1.0 - 0.001
