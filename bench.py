@@ -79,6 +79,29 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank values over the process group (the
+    slowest rank sets a step's time); the values unchanged on one process."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_qps(world, nq, ms):
+    """Whole-job queries/s: every rank searches its own nq queries per step."""
+    return world * nq / (ms / 1e3)
+
+
+def rank_query_seed(rank, base_seed):
+    """Each rank draws its own query batch (weak scaling); the base is shared."""
+    return base_seed + 1000 * rank
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -220,7 +243,7 @@ def main():
     # inputs: same base on every rank (a replica), a distinct query batch per rank
     W = WORKLOADS[args.workload]
     BUILD, L_GRID, K_RESULTS = W["build"], W["L_grid"], W["k"]
-    base, q = datagen.workload(args.workload, seed_query=datagen.SEED_QUERY + 1000 * rank)
+    base, q = datagen.workload(args.workload, seed_query=rank_query_seed(rank, datagen.SEED_QUERY))
     n, d = base.shape
     nq = len(q)
     bt = torch.from_numpy(base).cuda()
@@ -345,10 +368,8 @@ def main():
     rec_chosen_ties = (outs[kc]["d2"][:, :10] <= gt_d2[:, 9:10]).sum().item() / (10.0 * nq)
     ms_plain = timed(forms["plain"], plain_L, args.steps)
     rec_plain = recall10(outs[kq(plain_L)])
+    ms_step, ms_plain = max_over_ranks([ms_step, ms_plain], "cuda")
     if world > 1:
-        t = torch.tensor([ms_step, ms_plain], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step, ms_plain = t[0].item(), t[1].item()
         dist.barrier()
 
     # end to end through the public API with pinned host buffers
@@ -364,10 +385,7 @@ def main():
         ids_h.copy_(o["ids"], non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_ms = 1e3 * (time.perf_counter() - e2e_t0) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = t.item()
+    e2e_ms = max_over_ranks([e2e_ms], "cuda")[0]
 
     # batched uneven queries on the same index: k from {1, 10, 100}, L uniform
     # in 20..500, one autotuned persistent launch replayed as a CUDA graph,
@@ -386,9 +404,10 @@ def main():
     ev1.synchronize()
     ms_batched = ev0.elapsed_time(ev1) / args.steps
     ms_padded = timed(bprm, int(Lb.max()), max(2, args.steps // 2))
+    ms_batched, ms_padded = max_over_ranks([ms_batched, ms_padded], "cuda")
     batched = {"form": chosen_form.split("+")[0], "queries": nq, "k_choices": [1, 10, 100], "L_range": [20, 500],
-               "value": world * nq / (ms_batched / 1e3), "ms_per_step": ms_batched,
-               "padded_k100_L500": {"value": world * nq / (ms_padded / 1e3), "ms_per_step": ms_padded},
+               "value": job_qps(world, nq, ms_batched), "ms_per_step": ms_batched,
+               "padded_k100_L500": {"value": job_qps(world, nq, ms_padded), "ms_per_step": ms_padded},
                "plan": pinfo}
 
     peak, peak_kind = peaks()
@@ -406,7 +425,7 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": world * nq / (ms_step / 1e3), "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": job_qps(world, nq, ms_step), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"plain": "f32", "bf16": "bf16->f32", "fp8": "fp8e4m3->f32", "u8": "u8->i32"}[base_form],
@@ -416,12 +435,12 @@ def main():
                        "recall10": rec_chosen, "recall10_ties": rec_chosen_ties, "target_recall10": TARGET,
                        "parallelism": f"replicas{world}",
                        "l2": f"inputs larger than L2 ({base.nbytes >> 20} MB base)"},
-            "plain": {"value": world * nq / (ms_plain / 1e3), "ms_per_step": ms_plain, "L": plain_L,
+            "plain": {"value": job_qps(world, nq, ms_plain), "ms_per_step": ms_plain, "L": plain_L,
                       "recall10": rec_plain},
             "chosen_over_plain": ms_plain / ms_step,
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * nq / (e2e_ms / 1e3), "unit": UNIT,
+            "e2e": {"value": job_qps(world, nq, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": nq * d * 4, "d2h_bytes_per_step": nq * kc * 4},
             "gpu_launches": args.steps,
             "clocks": clocks,
