@@ -47,7 +47,8 @@ UNIT = "queries/s"
 TARGET = 0.95
 # Per workload: build parameters, the L grid, result size k, and a description.
 # `sift` is the headline configuration; `gist` (float, d=960) and `deep`
-# (10M x 96 unit vectors) are the precision and batched configurations.
+# (10M x 96 unit vectors) are the precision and batched configurations;
+# `rand4m` and `gauss5m` are the paper's own high-LID synthetic sets.
 WORKLOADS = {
     "sift": dict(build=dict(K=100, L=40, R=50, C=500), L_grid=list(range(100, 401, 25)), k=100,
                  desc="sift-shaped 1,000,000 x 128 int 0..255 GMM(100), 10,000 queries"),
@@ -55,6 +56,11 @@ WORKLOADS = {
                  k=100, desc="gist-shaped 1,000,000 x 960 f32 [0,1] GMM(50), 1,000 queries"),
     "deep": dict(build=dict(K=64, L=60, R=32, C=500), L_grid=[20, 40, 60, 100, 150, 200, 300, 400, 500, 700, 1000],
                  k=100, desc="deep-shaped 10,000,000 x 96 f32 unit-norm GMM(1000), 100,000 queries"),
+    # the paper's own synthetic sets (Table 1); R = 220 is the maximum out-degree it reports for them
+    "rand4m": dict(build=dict(K=100, L=60, R=220, C=500), L_grid=[20, 40, 60, 100, 150, 200, 300, 400, 500, 700, 1000],
+                   k=100, desc="RAND4M: 4,000,000 x 128 i.i.d. U(0,1), 10,000 queries"),
+    "gauss5m": dict(build=dict(K=100, L=60, R=220, C=500), L_grid=[20, 40, 60, 100, 150, 200, 300, 400, 500, 700, 1000],
+                    k=100, desc="GAUSS5M: 5,000,000 x 128 i.i.d. N(0,3), 10,000 queries"),
 }
 STOP_TRACE_LS, STOP_TRACE_CAP, STOP_ITERS = (100, 200, 400), 1024, 300
 STOP_THRESHOLDS = [0.9, 0.95, 0.98]

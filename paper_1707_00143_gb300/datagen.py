@@ -16,6 +16,12 @@ and value range of the dataset it stands in for:
              1,000 queries (GIST1M shape: D=960, real values).
 * ``deep``   10,000,000 x 96, unit-norm floats, 1,000 components, sigma 0.05,
              100,000 queries (DEEP shape: D=96).
+* ``rand4m`` 4,000,000 x 128, i.i.d. U(0, 1) coordinates, 10,000 queries (the
+             paper's RAND4M, Section 4.1.1).
+* ``gauss5m`` 5,000,000 x 128, i.i.d. N(0, 3) coordinates, read as variance 3
+             (standard deviation sqrt(3)), 10,000 queries (the paper's GAUSS5M;
+             a common scale factor changes no distance order, so the other
+             reading, sigma = 3, gives the same graph and results).
 
 Rows are generated in fixed-size chunks, each from its own generator seeded
 by ``(seed, chunk_index)``, so any row range can be regenerated on its own and
@@ -37,7 +43,7 @@ class Mixture:
     d: int
     n_components: int
     sigma: float
-    kind: str               # "int255" | "unit01" | "unitnorm"
+    kind: str               # "int255" | "unit01" | "unitnorm" | "uniform01" | "gauss"
     centre_lo: float = 0.0
     centre_hi: float = 1.0
     seed_centres: int = 3
@@ -48,6 +54,8 @@ WORKLOADS = {
     "sift": dict(mix=Mixture(128, 100, 30.0, "int255", 40.0, 215.0), n=1_000_000, nq=10_000),
     "gist": dict(mix=Mixture(960, 50, 0.1, "unit01", 0.2, 0.8), n=1_000_000, nq=1_000),
     "deep": dict(mix=Mixture(96, 1000, 0.05, "unitnorm"), n=10_000_000, nq=100_000),
+    "rand4m": dict(mix=Mixture(128, 1, 0.0, "uniform01"), n=4_000_000, nq=10_000),
+    "gauss5m": dict(mix=Mixture(128, 1, 3.0 ** 0.5, "gauss"), n=5_000_000, nq=10_000),
 }
 
 SEED_BASE = 1
@@ -65,6 +73,10 @@ def centres(mix: Mixture) -> np.ndarray:
 
 def _chunk(mix: Mixture, cen: np.ndarray, seed: int, chunk: int, rows: int) -> np.ndarray:
     rng = np.random.default_rng([seed, chunk])
+    if mix.kind == "uniform01":  # i.i.d. coordinates, no mixture
+        return rng.random((rows, mix.d), dtype=np.float64).astype(np.float32)
+    if mix.kind == "gauss":
+        return rng.normal(0.0, mix.sigma, size=(rows, mix.d)).astype(np.float32)
     comp = rng.integers(0, mix.n_components, size=rows)
     x = cen[comp] + rng.normal(0.0, mix.sigma, size=(rows, mix.d))
     if mix.kind == "int255":
