@@ -72,6 +72,8 @@ def _decl(L):
     L.orc_select_all.argtypes = [P, i32, P, i64, i32, i32, i32, i32, i32, i32, P, P]
     L.orc_build.argtypes = [P, i64, i32, i32, i32, i32, i32, u64, i32, P, P, P, P, P]
     L.orc_mrng_naive.argtypes = [P, i64, i32, P, P]
+    L.orc_build_naive.argtypes = [P, i64, i32, i32, i32, i32, P, P]
+    L.orc_search_random.argtypes = [P, P, i64, i32, P, i32, P, i64, i32, i32, i32, u64, i32, P, P, P, P]
     L.orc_recall_hits.argtypes = [P, i32, P, i32, i64, i32]
     L.orc_recall_hits.restype = i64
 
@@ -247,6 +249,37 @@ def build(base, K, L, R, Cap, seed=0, nthreads=None):
     _check(lib().orc_build(_p(base), n, d, K, L, R, Cap, seed, nthreads or nthreads_default(),
                            _p(adj), _p(deg), C.byref(nav), C.byref(added), _p(knn)), "build")
     return dict(adj=adj, deg=deg, nav=nav.value, n_added=added.value, knn=knn)
+
+
+def build_naive(base, K, R, nthreads=None):
+    """NSG-Naive (Section 4.1.2): MRNG edge selection over each node's K
+    nearest neighbours; no navigating node, no connectivity pass.  Returns
+    (adj [n][R] -1 padded, deg [n])."""
+    base = _f32(base)
+    n, d = base.shape
+    adj = np.empty((n, R), np.int32)
+    deg = np.empty(n, np.int32)
+    _check(lib().orc_build_naive(_p(base), n, d, K, R, nthreads or nthreads_default(), _p(adj), _p(deg)),
+           "build_naive")
+    return adj, deg
+
+
+def search_random(adj, base, queries, k, L, count, seed, deg=None, nthreads=1):
+    """Alg. 1 whose pool starts as the set of `count` seeded random nodes
+    (query q draws splitmix64(seed + q * 0x9e3779b97f4a7c15 + j) mod n, j < count).
+    Returns ids, dists, n_expand, n_dist like `search`."""
+    adj, base, queries = _i32(adj), _f32(base), _f32(queries)
+    n, width = adj.shape
+    d = base.shape[1]
+    dg = None if deg is None else _i32(deg)
+    nq = len(queries)
+    ids = np.empty((nq, k), np.int32)
+    dist = np.empty((nq, k), np.float32)
+    ne = np.empty(nq, np.int64)
+    nd = np.empty(nq, np.int64)
+    _check(lib().orc_search_random(_p(adj), _p(dg), n, width, _p(base), d, _p(queries), nq, k, L, count,
+                                   seed, nthreads, _p(ids), _p(dist), _p(ne), _p(nd)), "search_random")
+    return ids, dist, ne, nd
 
 
 def mrng_naive(base):

@@ -41,6 +41,9 @@
  *       out-degree < R gets the edge s->u; else the smallest reached id with
  *       out-degree < R; else error.  Then everything reachable from u is
  *       marked.
+ *   R10 NSG-Naive's "Alg. 1 with random initialization": the pool starts as
+ *       the set of `count` seeded random nodes (count <= L), query q drawing
+ *       splitmix64(seed + q * 0x9e3779b97f4a7c15 + j) mod n for j < count.
  */
 #include <math.h>
 #include <pthread.h>
@@ -351,18 +354,25 @@ static void vec_push(entry_vec *v, double dist, int32_t id) {
  * `trace` is given, the ids of S after each expansion are written to
  * trace[step][0..l) (-1 padded) for up to trace_steps steps.
  */
-static int32_t alg1(const graph *g, const metric *m, int32_t p, int32_t l, entry *S,
-                    uint8_t *visited, entry_vec *seen, int32_t *trace, int32_t trace_steps,
-                    int64_t *n_expand, int64_t *n_dist) {
+static int32_t alg1_from(const graph *g, const metric *m, const int32_t *init, int32_t n_init,
+                         int32_t l, entry *S, uint8_t *visited, entry_vec *seen, int32_t *trace,
+                         int32_t trace_steps, int64_t *n_expand, int64_t *n_dist) {
+    /* S starts as the set of the given nodes (duplicates once), sorted by key */
     int32_t size = 0;
-    double dp = metric_dist(m, p);
-    S[size].dist = dp;
-    S[size].id = p;
-    S[size].checked = 0;
-    size++;
-    visited[p] = 1;
-    *n_dist += 1;
-    if (seen) vec_push(seen, dp, p);
+    for (int32_t t = 0; t < n_init; ++t) {
+        int32_t p = init[t];
+        if (visited[p]) continue;
+        visited[p] = 1;
+        double dp = metric_dist(m, p);
+        *n_dist += 1;
+        if (seen) vec_push(seen, dp, p);
+        S[size].dist = dp;
+        S[size].id = p;
+        S[size].checked = 0;
+        size++;
+    }
+    qsort(S, size, sizeof(entry), entry_cmp);
+    if (size > l) size = l;
     int64_t step = 0;
     for (;;) {
         int32_t i = 0;
@@ -392,6 +402,12 @@ static int32_t alg1(const graph *g, const metric *m, int32_t p, int32_t l, entry
         step++;
     }
     return size;
+}
+
+static int32_t alg1(const graph *g, const metric *m, int32_t p, int32_t l, entry *S,
+                    uint8_t *visited, entry_vec *seen, int32_t *trace, int32_t trace_steps,
+                    int64_t *n_expand, int64_t *n_dist) {
+    return alg1_from(g, m, &p, 1, l, S, visited, seen, trace, trace_steps, n_expand, n_dist);
 }
 
 static int32_t graph_max_width(const graph *g) { return g->lazy ? g->lazy->k : g->width; }
@@ -433,6 +449,52 @@ int orc_search(const int32_t *adj, const int32_t *deg, int64_t n, int32_t width,
         return ORC_EINVAL;
     search_ctx c = {{adj, deg, width, NULL}, base, qry, n, d, start, l, k, ids, dist, n_expand, n_dist};
     run_units(search_unit, &c, nq, nthreads);
+    return ORC_OK;
+}
+
+/* Alg. 1 with random initialisation (NSG-Naive, Section 4.1.2; reading R10):
+ * query qi's pool starts as the set of nodes
+ *   splitmix64(seed + qi * 0x9e3779b97f4a7c15 + j) mod n,  j = 0 .. count-1
+ * (repeats once), then Alg. 1 runs as usual. */
+uint64_t orc_splitmix64(uint64_t x);
+
+typedef struct {
+    search_ctx s;
+    int32_t count;
+    uint64_t seed;
+} search_rand_ctx;
+
+static void search_rand_unit(void *p, int64_t qi) {
+    search_rand_ctx *c = (search_rand_ctx *)p;
+    entry *S = (entry *)malloc(sizeof(entry) * (c->s.l + c->count + graph_max_width(&c->s.g) + 1));
+    uint8_t *visited = (uint8_t *)calloc((size_t)c->s.n, 1);
+    int32_t *init = (int32_t *)malloc(sizeof(int32_t) * c->count);
+    for (int32_t j = 0; j < c->count; ++j)
+        init[j] = (int32_t)(orc_splitmix64(c->seed + (uint64_t)qi * 0x9e3779b97f4a7c15ULL + (uint64_t)j) %
+                            (uint64_t)c->s.n);
+    metric m = {c->s.base, c->s.d, c->s.qry + qi * c->s.d, NULL};
+    int64_t ne = 0, nd = 0;
+    int32_t size = alg1_from(&c->s.g, &m, init, c->count, c->s.l, S, visited, NULL, NULL, 0, &ne, &nd);
+    for (int32_t t = 0; t < c->s.k; ++t) {
+        c->s.ids[qi * c->s.k + t] = t < size ? S[t].id : -1;
+        if (c->s.dist) c->s.dist[qi * c->s.k + t] = t < size ? (float)S[t].dist : INFINITY;
+    }
+    if (c->s.n_expand) c->s.n_expand[qi] = ne;
+    if (c->s.n_dist) c->s.n_dist[qi] = nd;
+    free(init);
+    free(S);
+    free(visited);
+}
+
+int orc_search_random(const int32_t *adj, const int32_t *deg, int64_t n, int32_t width,
+                      const float *base, int32_t d, const float *qry, int64_t nq, int32_t k, int32_t l,
+                      int32_t count, uint64_t seed, int32_t nthreads, int32_t *ids, float *dist,
+                      int64_t *n_expand, int64_t *n_dist) {
+    if (!adj || !base || !qry || !ids || n < 1 || d < 1 || k < 1 || l < 1 || count < 1 || count > l)
+        return ORC_EINVAL;
+    search_rand_ctx c = {{{adj, deg, width, NULL}, base, qry, n, d, 0, l, k, ids, dist, n_expand, n_dist},
+                         count, seed};
+    run_units(search_rand_unit, &c, nq, nthreads);
     return ORC_OK;
 }
 
@@ -717,6 +779,22 @@ int orc_build(const float *base, int64_t n, int32_t d, int32_t K, int32_t l, int
     *nav_out = nav;
     if (!knn_out) free(knn);
     free(c);
+    return rc;
+}
+
+/* NSG-Naive (Section 4.1.2): the MRNG edge selection applied directly to the
+ * edges of the kNN graph (each node's K nearest, in key order, are its
+ * candidates); no navigating node, no connectivity pass. */
+int orc_build_naive(const float *base, int64_t n, int32_t d, int32_t K, int32_t R, int32_t nthreads,
+                    int32_t *adj, int32_t *deg) {
+    if (!base || !adj || !deg || n < 2 || d < 1 || K < 1 || K >= n || R < 1) return ORC_EINVAL;
+    int32_t *knn = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * K);
+    float *kd = (float *)malloc(sizeof(float) * (size_t)n * K);
+    int rc = orc_knn_rows(base, n, d, K, NULL, n, nthreads, knn, kd);
+    for (int64_t v = 0; !rc && v < n; ++v)
+        deg[v] = mrng_select(base, d, knn + v * K, kd + v * K, K, R, adj + v * R);
+    free(knn);
+    free(kd);
     return rc;
 }
 
