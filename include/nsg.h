@@ -67,6 +67,11 @@ typedef struct {
     int32_t stop_k;        /* result size the stop rule protects (<= 0 -> min(k, 10)) */
     int32_t stop_min_steps; /* never stop before this many expansions; the rule is
                                evaluated at min_steps, min_steps + 4, min_steps + 8, ... */
+    int32_t init_random;   /* > 0: the pool starts as the set of this many seeded random
+                              nodes (<= L) instead of the navigating node: query q draws
+                              splitmix64(init_seed + q * 0x9e3779b97f4a7c15 + j) mod n,
+                              j < init_random (NSG-Naive's random initialisation) */
+    uint64_t init_seed;
 } nsg_search_params;
 
 /* Parameters of the early-termination MLP (8 features -> 64 ReLU -> 1):
@@ -208,9 +213,19 @@ nsg_status nsg_connect(const float *base_dev, int64_t n, int32_t d, int32_t *adj
 nsg_status nsg_build(const float *base_dev, int64_t n, int32_t d, int32_t K, int32_t L, int32_t R,
                      int32_t C, uint64_t seed, void *stream, nsg_index **out);
 
+/* NSG-Naive (Section 4.1.2; the paper's ablation baseline): the MRNG edge
+ *   selection applied directly to each node's K nearest neighbours (A1 then
+ *   A6), with no navigating node and no connectivity pass.  The index's start
+ *   node is splitmix64(seed) mod n; search it with params->init_random > 0
+ *   for the paper's random initialisation.  K <= 256, R <= 1024.
+ *   Synchronises the stream. */
+nsg_status nsg_build_naive(const float *base_dev, int64_t n, int32_t d, int32_t K, int32_t R, uint64_t seed,
+                           void *stream, nsg_index **out);
+
 /* An index over a given graph (for searching a graph built elsewhere).
- *   adj_dev [n][R] (-1 padded rows without repeated ids), deg_dev [n]
- *   nullable (counted from adj when NULL).  Base and graph are copied. */
+ *   adj_dev [n][R] (-1 padded; a row may list an id more than once, it is
+ *   visited once), deg_dev [n] nullable (counted from adj when NULL).  Base
+ *   and graph are copied. */
 nsg_status nsg_index_from_graph(const float *base_dev, int64_t n, int32_t d, const int32_t *adj_dev,
                                 const int32_t *deg_dev, int32_t R, int32_t nav, void *stream,
                                 nsg_index **out);

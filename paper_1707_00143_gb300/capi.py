@@ -33,13 +33,14 @@ class NsgError(RuntimeError):
 class SearchParams(C.Structure):
     _fields_ = [("max_steps", C.c_int32), ("hash_slots", C.c_int32), ("precision", C.c_int32),
                 ("warps_per_cta", C.c_int32), ("rerank", C.c_int32), ("stop_model", C.c_void_p),
-                ("stop_threshold", C.c_float), ("stop_k", C.c_int32), ("stop_min_steps", C.c_int32)]
+                ("stop_threshold", C.c_float), ("stop_k", C.c_int32), ("stop_min_steps", C.c_int32),
+                ("init_random", C.c_int32), ("init_seed", C.c_uint64)]
 
     def __init__(self, max_steps=0, hash_slots=0, precision=0, warps_per_cta=0, rerank=-1, stop_model=None,
-                 stop_threshold=0.5, stop_k=0, stop_min_steps=0):
+                 stop_threshold=0.5, stop_k=0, stop_min_steps=0, init_random=0, init_seed=0):
         ptr = stop_model.data_ptr() if isinstance(stop_model, torch.Tensor) else stop_model
         super().__init__(max_steps, hash_slots, precision, warps_per_cta, rerank, ptr, stop_threshold, stop_k,
-                         stop_min_steps)
+                         stop_min_steps, init_random, init_seed)
 
 
 STOP_FEATURES, STOP_PARAMS = 8, 641
@@ -74,6 +75,7 @@ SIGNATURES = [
     ("nsg_prune", [P, i64, i32, P, P, P, i32, i32, i64, i64, P, P, P], i32),
     ("nsg_connect", [P, i64, i32, P, P, i32, i32, i32, P, P], i32),
     ("nsg_build", [P, i64, i32, i32, i32, i32, i32, u64, P, P], i32),
+    ("nsg_build_naive", [P, i64, i32, i32, i32, u64, P, P], i32),
     ("nsg_index_from_graph", [P, i64, i32, P, P, i32, i32, P, P], i32),
     ("nsg_search", [P, P, i64, i32, i32, P, P, P], i32),
     ("nsg_search_ex", [P, P, i64, i32, i32, P, P, P, P, P, P, P], i32),
@@ -362,6 +364,16 @@ class Plan:
                 lib().nsg_plan_free(self.h)
         except Exception:
             pass
+
+
+def nsg_build_naive(base, K, R, seed=0):
+    """NSG-Naive: MRNG selection over the kNN graph's edges (no navigating
+    node, no connectivity pass); search it with SearchParams(init_random=...)."""
+    base = _dev(base, torch.float32)
+    n, d = base.shape
+    h = C.c_void_p()
+    _check(lib().nsg_build_naive(_ptr(base), n, d, K, R, seed, _stream(), C.byref(h)), "nsg_build_naive")
+    return Index(h)
 
 
 def nsg_build(base, K, L, R, Cap, seed=0):

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256) prune_kernel(PruneArgs a) {
         const int64_t v = a.v0 + j;
         const int *ci = a.cand_ids + j * a.C;
         const float *cd = a.cand_d2 + j * a.C;
-        const int cnt = min(max(a.cand_count[j], 0), a.C);
+        const int cnt = a.cand_count != nullptr ? min(max(a.cand_count[j], 0), a.C) : a.C;
         int nk = 0;
         if (cnt > 0) {
             if (lane == 0) kept[0] = ci[0];

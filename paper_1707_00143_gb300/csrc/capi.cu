@@ -485,6 +485,72 @@ nsg_status nsg_connect(const float *base_dev, int64_t n, int32_t d, int32_t *adj
     return connect_run(base_dev, n, d, adj_dev, deg_dev, R, nav, L, n_added_host, st);
 }
 
+nsg_status nsg_build_naive(const float *base_dev, int64_t n, int32_t d, int32_t K, int32_t R, uint64_t seed,
+                           void *stream, nsg_index **out) {
+    if (!out) return NSG_EINVAL;
+    *out = nullptr;
+    if (!base_dev || n < 2 || n >= INT32_MAX || d < 1 || d > 4 * nsg::MAX_DP4_HOST || K < 1 || K >= n ||
+        K > 256 || R < 1 || R > 1024)
+        return NSG_EINVAL;
+    cudaStream_t st = S(stream);
+    auto t_all = std::chrono::steady_clock::now();
+    nsg_index *ix = new (std::nothrow) nsg_index;
+    if (!ix) return NSG_ENOMEM;
+    ix->n = n;
+    ix->d = d;
+    ix->dp = round_up4(d);
+    ix->R = R;
+    DevBuf<float> base, kd;
+    DevBuf<int> adj, deg, knn;
+    nsg_status s = padded_copy(base_dev, n, d, ix->dp, base, st);
+    cudaError_t e = cudaSuccess;
+    if (!s && (e = adj.alloc((size_t)n * R)) != cudaSuccess) s = cuda_fail(e, "alloc adj");
+    if (!s && (e = deg.alloc((size_t)n)) != cudaSuccess) s = cuda_fail(e, "alloc deg");
+    if (!s && (e = knn.alloc((size_t)n * K)) != cudaSuccess) s = cuda_fail(e, "alloc knn");
+    if (!s && (e = kd.alloc((size_t)n * K)) != cudaSuccess) s = cuda_fail(e, "alloc knn d2");
+    // the kNN graph (ids and distances, in key order per row) ...
+    auto t0 = std::chrono::steady_clock::now();
+    if (!s) s = knn_run(base.p, n, ix->dp, base.p, n, 0, K, 1, knn.p, kd.p, st);
+    if (!s && (e = cudaStreamSynchronize(st)) != cudaSuccess) s = cuda_fail(e, "knn");
+    ix->ms[0] = (float)since_ms(t0);
+    // ... whose rows are every node's candidates for the MRNG selection
+    t0 = std::chrono::steady_clock::now();
+    if (!s) {
+        nsg::PruneLaunch p;
+        p.base = base.p;
+        p.n = n;
+        p.dp = ix->dp;
+        p.cand_ids = knn.p;
+        p.cand_d2 = kd.p;
+        p.cand_count = nullptr;
+        p.C = K;
+        p.R = R;
+        p.v0 = 0;
+        p.nv = n;
+        p.adj = adj.p;
+        p.deg = deg.p;
+        if ((e = nsg::launch_prune(p, st)) != cudaSuccess) s = cuda_fail(e, "launch_prune");
+        if (!s && (e = cudaStreamSynchronize(st)) != cudaSuccess) s = cuda_fail(e, "prune");
+    }
+    ix->ms[3] = (float)since_ms(t0);
+    ix->nav = (int)(splitmix64(seed) % (uint64_t)n);  // a random start node; no navigating node
+    if (s) {
+        destroy(ix);
+        return s;
+    }
+    ix->base = base.release();
+    ix->adj = adj.release();
+    ix->deg = deg.release();
+    s = finish_index(ix, st);
+    ix->ms[5] = (float)since_ms(t_all);
+    if (s) {
+        destroy(ix);
+        return s;
+    }
+    *out = ix;
+    return NSG_OK;
+}
+
 nsg_status nsg_build(const float *base_dev, int64_t n, int32_t d, int32_t K, int32_t L, int32_t R,
                      int32_t C, uint64_t seed, void *stream, nsg_index **out) {
     if (!out) return NSG_EINVAL;
@@ -623,9 +689,10 @@ nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t n
                        int32_t *n_dist_dev, int32_t *status_dev, nsg::SearchLaunch &l) {
     if (!idx || k < 1 || L < k || L > 1024 || nq < 0 || nq >= INT32_MAX) return NSG_EINVAL;
     if (nq > 0 && (!queries_dev || !ids_dev)) return NSG_EINVAL;
-    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0};
+    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0, 0, 0};
     if (params) p = *params;
     if (p.precision < NSG_PREC_F32 || p.precision > NSG_PREC_U8) return NSG_EINVAL;
+    if (p.init_random < 0 || p.init_random > L) return NSG_EINVAL;
     if (p.precision != NSG_PREC_F32 && !idx->lowp[p.precision]) return NSG_EINVAL;  // nsg_index_prepare first
     if (p.hash_slots > 0 && (p.hash_slots < 64 || (p.hash_slots & (p.hash_slots - 1)) || p.hash_slots > 65536))
         return NSG_EINVAL;
@@ -656,6 +723,8 @@ nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t n
     l.n_dist = n_dist_dev;
     l.status = status_dev;
     l.any_capped = nullptr;
+    l.init_count = p.init_random;
+    l.init_seed = p.init_seed;
     if (p.precision != NSG_PREC_F32) {
         l.precision = p.precision;
         l.lowp = idx->lowp[p.precision];
@@ -872,7 +941,7 @@ nsg_status nsg_search_trace(const nsg_index *idx, const float *queries_dev, int6
                             const nsg_search_params *params, int32_t *ids_dev, float *feat_dev,
                             uint8_t *flag_dev, int32_t *steps_dev, int32_t cap, void *stream) {
     if (cap < 1 || (nq > 0 && (!feat_dev || !flag_dev || !steps_dev))) return NSG_EINVAL;
-    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0};
+    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0, 0, 0};
     if (params) p = *params;
     p.stop_model = nullptr;  // traces record the fixed-L search
     nsg::SearchLaunch l;

@@ -44,6 +44,9 @@ struct SearchLaunch {
     // visiting order, device work counter (reset before each launch)
     const int *kv = nullptr, *Lv = nullptr, *order = nullptr;
     int *work = nullptr;
+    // random initial pool of init_count seeded draws (0: start at `start`)
+    int init_count = 0;
+    uint64_t init_seed = 0;
 };
 cudaError_t launch_search(const SearchLaunch &a, cudaStream_t st);
 
@@ -97,7 +100,7 @@ struct PruneLaunch {
     int dp;
     const int *cand_ids;
     const float *cand_d2;
-    const int *cand_count;
+    const int *cand_count;  // nullptr: every row holds C candidates
     int C, R;
     int64_t v0, nv;
     int *adj;

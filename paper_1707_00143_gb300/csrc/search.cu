@@ -68,6 +68,10 @@ struct SearchArgs {
     // persistent warps draw from (nullptr: static grid-stride assignment)
     const int *kv, *Lv, *order;
     int *work;
+    // random initial pool (count 0: start at `start`), base rows n
+    int init_count;
+    uint64_t init_seed;
+    int n;
 };
 
 // Alg. 1 per query.  P = PREC_F32: distances on the FP32 rows (the plain
@@ -114,6 +118,8 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
         sc.trace_flag = a.trace_flag != nullptr ? a.trace_flag + qi * (int64_t)a.trace_cap : nullptr;
         sc.trace_cap = a.trace_cap;
         const StopCtx *scp = STOP ? &sc : nullptr;
+        const InitRand ir{a.init_count < Lq ? a.init_count : Lq, a.init_seed, qi, a.n};
+        const InitRand *initp = a.init_count > 0 ? &ir : nullptr;
         SearchOut o;
         bool rerank = a.rerank == 1;
         if constexpr (P == PREC_F32) {
@@ -121,7 +127,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
             dist.Q.load(qp, a.d, a.dp4);
             o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, Lq, s,
                                                               (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
-                                                              csize, nullptr, 0, scp);
+                                                              csize, nullptr, 0, scp, nullptr, initp);
         } else if constexpr (P == PREC_U8) {
             // an 8-bit row is a quarter of the FP32 row: G8 lanes of up to
             // NSG_U8CHUNKS 16-byte chunks each, 32 / G8 rows per pass
@@ -133,7 +139,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
             rerank = rerank || (a.rerank == 2 && !qexact);
             o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, Lq, s,
                                                               (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
-                                                              csize, nullptr, 0, scp);
+                                                              csize, nullptr, 0, scp, nullptr, initp);
         } else {
             constexpr int VC = (V * 4) / PrecEpc<P>::value > 0 ? (V * 4) / PrecEpc<P>::value : 1;
             // rows in flight per group: a low-precision row costs VC*4 registers per lane
@@ -142,7 +148,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
             dist.Q.load(qp, a.d, a.scale);
             o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, Lq, s,
                                                               (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
-                                                              csize, nullptr, 0, scp);
+                                                              csize, nullptr, 0, scp, nullptr, initp);
         }
         const uint64_t *res = s.pool;
         int rsize = o.size;
@@ -323,6 +329,9 @@ cudaError_t launch_search(const SearchLaunch &l, cudaStream_t st) {
     a.Lv = l.Lv;
     a.order = l.order;
     a.work = l.work;
+    a.init_count = l.init_count;
+    a.init_seed = l.init_seed;
+    a.n = (int)l.n;
     size_t per_warp = warp_smem_bytes(a.L, a.W, a.C, a.H);
     const size_t per_cta = l.stop_model ? ((sizeof(StopMLP) + 15) & ~size_t(15)) : 0;
     cudaError_t err = cudaSuccess;

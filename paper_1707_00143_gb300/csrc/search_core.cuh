@@ -154,12 +154,31 @@ struct DistF32 {
     }
 };
 
+// Seeded random initial pool (NSG-Naive's "Alg. 1 with random
+// initialization"): query qi starts from the set of nodes
+// splitmix64(seed + qi * 0x9e3779b97f4a7c15 + j) mod n, j < count (count <= L).
+struct InitRand {
+    int count;
+    uint64_t seed;
+    int64_t qi;
+    int n;
+};
+
+// Published SplitMix64 finaliser (Steele, Lea, Flood 2014).
+__device__ __forceinline__ uint64_t splitmix64_dev(uint64_t x) {
+    uint64_t z = x + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
 // `dist(ids, m, keys)` writes keys[c] = (d2(query, row ids[c]), ids[c]) for c < m.
 // STOP: compile the learned-stop / trace hooks (stop must then be non-null).
 template <bool COLLECT, bool COHERENT, class D, bool STOP = false>
 __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, WarpSmem &s, uint32_t hmask,
                                int hshift, int max_steps, int excl, int C, int &csize, int *xlog = nullptr,
-                               int xcap = 0, const StopCtx *stop = nullptr, uint64_t *xthr = nullptr) {
+                               int xcap = 0, const StopCtx *stop = nullptr, uint64_t *xthr = nullptr,
+                               const InitRand *init = nullptr) {
     const unsigned lane = lane_id();
     SearchOut o;
     o.size = 0;
@@ -170,17 +189,39 @@ __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, Warp
     int since_change = 0, last_m = 0;
     bool last_changed = true;
     hash_clear(s.hash, (int)hmask + 1);
-    if (lane == 0) {
-        visit(s.hash, hmask, hshift, start);
-        s.ids[0] = start;
+    if (init != nullptr && init->count > 0) {
+        // the pool starts as the set of the drawn nodes, 32 draws at a time
+        for (int b = 0; b < init->count; b += 32) {
+            const int j = b + (int)lane;
+            const int v = j < init->count
+                              ? (int)(splitmix64_dev(init->seed + (uint64_t)init->qi * 0x9e3779b97f4a7c15ull +
+                                                     (uint64_t)j) %
+                                      (uint64_t)init->n)
+                              : -1;
+            const bool fresh = v >= 0 && visit(s.hash, hmask, hshift, v);
+            const unsigned bal = __ballot_sync(NSG_FULL, fresh);
+            if (fresh) s.ids[__popc(bal & lanemask_lt())] = v;
+            const int m = __popc(bal);
+            __syncwarp();
+            if (m > 0) {
+                dist(s.ids, m, s.keys);
+                o.n_dist += m;
+                warp_merge(s.pool, L, o.size, s.keys, m, s.ck, s.cp, s.sk, s.sp);
+            }
+        }
+    } else {
+        if (lane == 0) {
+            visit(s.hash, hmask, hshift, start);
+            s.ids[0] = start;
+        }
+        __syncwarp();
+        dist(s.ids, 1, s.keys);
+        o.n_dist = 1;
+        if (lane == 0) s.pool[0] = s.keys[0];
+        __syncwarp();
+        o.size = 1;
+        if (COLLECT) collect_merge(s, 1, excl, C, csize);
     }
-    __syncwarp();
-    dist(s.ids, 1, s.keys);
-    o.n_dist = 1;
-    if (lane == 0) s.pool[0] = s.keys[0];
-    __syncwarp();
-    o.size = 1;
-    if (COLLECT) collect_merge(s, 1, excl, C, csize);
     int cursor = 0;
     for (;;) {
         int i = -1;
