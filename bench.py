@@ -75,6 +75,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="sift", choices=sorted(WORKLOADS))
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    p.add_argument("--naive", action="store_true", help="also build and sweep NSG-Naive (ablation)")
     return p.parse_args()
 
 
@@ -393,6 +394,31 @@ def main():
     e2e_ms = 1e3 * (time.perf_counter() - e2e_t0) / args.steps
     e2e_ms = max_over_ranks([e2e_ms], "cuda")[0]
 
+    # NSG-Naive (Section 4.1.2, the paper's ablation): MRNG selection over the
+    # kNN graph's edges, no navigating node or connectivity pass, searched by
+    # Alg. 1 from L random nodes; the plain form at a few pool sizes
+    naive = None
+    if args.naive:
+        t2 = time.perf_counter()
+        nidx = capi.nsg_build_naive(bt, BUILD["K"], BUILD["R"], seed=0)
+        torch.cuda.synchronize()
+        nb_s = time.perf_counter() - t2
+        npts = []
+        for Ln in L_GRID[:: max(1, len(L_GRID) // 5)]:
+            nprm = capi.SearchParams(0, 0, capi.PREC_F32, 0, -1, None, 0.5, 0, 0, Ln, 1)
+            o = nidx.search_ex(qt, kq(Ln), Ln, params=nprm, counters=False)
+            torch.cuda.synchronize()
+            ev0.record(st)
+            for _ in range(2):
+                o = nidx.search_ex(qt, kq(Ln), Ln, params=nprm, out=o, counters=False)
+            ev1.record(st)
+            ev1.synchronize()
+            npts.append({"L": Ln, "recall10": recall10(o), "qps": nq / (ev0.elapsed_time(ev1) / 2 / 1e3)})
+        ninfo = nidx.info()
+        naive = {"build_seconds": nb_s, "avg_degree": ninfo["avg_degree"], "init": "L random nodes",
+                 "sweep": npts, "nsg_plain_sweep": sweeps["plain"]}
+        del nidx
+
     # batched uneven queries on the same index: k from {1, 10, 100}, L uniform
     # in 20..500, one autotuned persistent launch replayed as a CUDA graph,
     # against the same batch padded to one fixed (k, L) = (100, 500) launch
@@ -459,6 +485,7 @@ def main():
                       "fp8_scale": info["fp8_scale"]},
             "per_query": {"n_expand": n_expand / nq, "n_dist": n_dist / nq},
             "batched": batched,
+            "nsg_naive": naive,
             "learned_stop": {"train_queries": nq, "trace_L": list(STOP_TRACE_LS), "iters": STOP_ITERS,
                              "train_seconds": train_s, "loss_first": stop_loss[0].item(),
                              "loss_last": stop_loss[-1].item(), "thresholds": STOP_THRESHOLDS},
