@@ -26,6 +26,15 @@
 #ifndef NSG_U8CHUNKS
 #define NSG_U8CHUNKS 2
 #endif
+#ifndef NSG_U8ROWS_WIDE
+#define NSG_U8ROWS_WIDE 8
+#endif
+#ifndef NSG_UL_WIDE
+#define NSG_UL_WIDE 4
+#endif
+#ifndef NSG_U_RERANK_WIDE
+#define NSG_U_RERANK_WIDE 3
+#endif
 
 namespace nsg {
 
@@ -134,7 +143,10 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
             constexpr int VG = V * G;  // FP32 float4 capacity of a lane group
             constexpr int G8 = VG / (4 * NSG_U8CHUNKS) < 1 ? 1 : (VG / (4 * NSG_U8CHUNKS) > 32 ? 32 : VG / (4 * NSG_U8CHUNKS));
             constexpr int VC = VG / (4 * G8);
-            DistU8<G8, VC, NSG_U8ROWS> dist{{}, a.lowp, a.dc};
+            // rows of 513..1024 values run with the default register budget:
+            // more of them in flight
+            constexpr int U8R = V == 8 ? NSG_U8ROWS_WIDE : (V > 8 ? 2 : NSG_U8ROWS);
+            DistU8<G8, VC, U8R> dist{{}, a.lowp, a.dc};
             const bool qexact = dist.Q.load(qp, a.d, a.lo, a.scale);
             rerank = rerank || (a.rerank == 2 && !qexact);
             o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, Lq, s,
@@ -143,7 +155,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
         } else {
             constexpr int VC = (V * 4) / PrecEpc<P>::value > 0 ? (V * 4) / PrecEpc<P>::value : 1;
             // rows in flight per group: a low-precision row costs VC*4 registers per lane
-            constexpr int UL = VC <= 1 ? NSG_UL1 : (VC == 2 ? NSG_UL2 : 2);
+            constexpr int UL = V == 8 ? NSG_UL_WIDE : (VC <= 1 ? NSG_UL1 : (VC == 2 ? NSG_UL2 : 2));
             DistLp<P, G, VC, UL> dist{{}, a.lowp, a.dc};
             dist.Q.load(qp, a.d, a.scale);
             o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, Lq, s,
@@ -152,9 +164,12 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
         }
         const uint64_t *res = s.pool;
         int rsize = o.size;
-        if (P != PREC_F32 && rerank) {
+        if constexpr (P != PREC_F32) if (rerank) {
             uint64_t *cl = a.C > 0 ? s.clist : reinterpret_cast<uint64_t *>(s.hash);
-            DistF32<G, V, U> exact{{}, a.base4, a.dp4};
+            // the re-rank gathers all L pool rows at once: more rows in flight
+            // than the traversal for rows of 513..1024 values
+            constexpr int UR = V == 8 ? NSG_U_RERANK_WIDE : U;
+            DistF32<G, V, UR> exact{{}, a.base4, a.dp4};
             exact.Q.load(qp, a.d, a.dp4);
             int kept = 0;
             for (int c0 = 0; c0 < o.size; c0 += a.W) {

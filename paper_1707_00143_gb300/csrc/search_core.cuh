@@ -27,6 +27,10 @@
 #ifndef NSG_PF_ROWS
 #define NSG_PF_ROWS 1
 #endif
+// FP32 rows in flight per lane group for rows of 513..1024 values
+#ifndef NSG_U_WIDE8
+#define NSG_U_WIDE8 2
+#endif
 
 namespace nsg {
 
@@ -358,7 +362,7 @@ __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, Warp
             constexpr int G_ = 32, V_ = 4, U_ = 2;                              \
             __VA_ARGS__;                                                        \
         } else if ((dp4) <= 256) {                                              \
-            constexpr int G_ = 32, V_ = 8, U_ = 2;                              \
+            constexpr int G_ = 32, V_ = 8, U_ = NSG_U_WIDE8;                    \
             __VA_ARGS__;                                                        \
         } else {                                                                \
             constexpr int G_ = 32, V_ = 16, U_ = 1;                             \

@@ -262,6 +262,14 @@ def test_wide_rows_search_bit_exact(nsg, d, hi):
     assert np.array_equal(H(out["d2"]), rd2)
     assert np.array_equal(H(out["n_expand"]), rne)
     assert np.array_equal(H(out["n_dist"]), rnd)
+    # the low-precision wide kernels: BF16 and 8-bit copies hold these values
+    # exactly and their sums stay below 2^24, so the traversal keys are the
+    # FP32 ones and, with the FP32 re-rank, so are the results
+    for prec in (nsg.PREC_BF16, nsg.PREC_U8):
+        idx.prepare(prec)
+        lp = idx.search_ex(T(q), 10, 48, params=nsg.SearchParams(0, 16384, prec, 0, 1))
+        assert np.array_equal(H(lp["ids"]), rid) and np.array_equal(H(lp["d2"]), rd2)
+        assert np.array_equal(H(lp["n_expand"]), rne)
     # and the GPU build of the same rows equals the oracle's graph
     g = nsg.nsg_build(T(base), 12, 30, 12, 100, seed=0)
     adj, deg = g.graph()
