@@ -72,6 +72,9 @@ typedef struct {
                               splitmix64(init_seed + q * 0x9e3779b97f4a7c15 + j) mod n,
                               j < init_random (NSG-Naive's random initialisation) */
     uint64_t init_seed;
+    int32_t warps_per_query; /* 1 (default), 2 or 4 warps share each query: the same
+                                steps and results, more rows in flight per expansion
+                                (not with a stop model or a trace) */
 } nsg_search_params;
 
 /* Parameters of the early-termination MLP (8 features -> 64 ReLU -> 1):
@@ -268,8 +271,10 @@ nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t
  * nsg_search_batched: one-shot form (derives the visiting order each call).
  * nsg_plan_create: binds an index, the query / k / L / output buffers and
  *   the parameters; derives the visiting order; with `autotune` times the
- *   candidate launch shapes (warps per block 2/4/8 x visited-hash slots
- *   512/1024/2048) on the bound batch and keeps the fastest; then captures
+ *   candidate launch shapes (warps per query 1/2/4 x warps per block 2/4/8 x
+ *   visited-hash slots 512/1024/2048; shapes with fewer warps per block than
+ *   per query skipped, 24 in all) on the bound batch and keeps the fastest;
+ *   then captures
  *   "reset work counter + search" as a CUDA graph.  Synchronises.
  * nsg_plan_run: replays the graph on `stream` (asynchronous).
  * nsg_plan_info: the chosen shape and the tuning timings.
@@ -281,6 +286,7 @@ typedef struct {
     int32_t n_tried;       /* shapes timed by the autotuner (0: none) */
     float best_ms;         /* time of one run of the chosen shape (autotune only) */
     float worst_ms;        /* slowest shape tried */
+    int32_t warps_per_query; /* chosen warps per query */
 } nsg_plan_info_t;
 
 nsg_status nsg_search_batched(const nsg_index *idx, const float *queries_dev, int64_t nq, const int32_t *k_dev,

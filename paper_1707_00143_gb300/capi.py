@@ -34,13 +34,13 @@ class SearchParams(C.Structure):
     _fields_ = [("max_steps", C.c_int32), ("hash_slots", C.c_int32), ("precision", C.c_int32),
                 ("warps_per_cta", C.c_int32), ("rerank", C.c_int32), ("stop_model", C.c_void_p),
                 ("stop_threshold", C.c_float), ("stop_k", C.c_int32), ("stop_min_steps", C.c_int32),
-                ("init_random", C.c_int32), ("init_seed", C.c_uint64)]
+                ("init_random", C.c_int32), ("init_seed", C.c_uint64), ("warps_per_query", C.c_int32)]
 
     def __init__(self, max_steps=0, hash_slots=0, precision=0, warps_per_cta=0, rerank=-1, stop_model=None,
-                 stop_threshold=0.5, stop_k=0, stop_min_steps=0, init_random=0, init_seed=0):
+                 stop_threshold=0.5, stop_k=0, stop_min_steps=0, init_random=0, init_seed=0, warps_per_query=1):
         ptr = stop_model.data_ptr() if isinstance(stop_model, torch.Tensor) else stop_model
         super().__init__(max_steps, hash_slots, precision, warps_per_cta, rerank, ptr, stop_threshold, stop_k,
-                         stop_min_steps, init_random, init_seed)
+                         stop_min_steps, init_random, init_seed, warps_per_query)
 
 
 STOP_FEATURES, STOP_PARAMS = 8, 641
@@ -325,7 +325,7 @@ class Index:
 
 class PlanInfo(C.Structure):
     _fields_ = [("warps_per_cta", C.c_int32), ("hash_slots", C.c_int32), ("n_tried", C.c_int32),
-                ("best_ms", C.c_float), ("worst_ms", C.c_float)]
+                ("best_ms", C.c_float), ("worst_ms", C.c_float), ("warps_per_query", C.c_int32)]
 
 
 class Plan:

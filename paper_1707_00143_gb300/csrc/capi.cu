@@ -689,10 +689,12 @@ nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t n
                        int32_t *n_dist_dev, int32_t *status_dev, nsg::SearchLaunch &l) {
     if (!idx || k < 1 || L < k || L > 1024 || nq < 0 || nq >= INT32_MAX) return NSG_EINVAL;
     if (nq > 0 && (!queries_dev || !ids_dev)) return NSG_EINVAL;
-    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0, 0, 0};
+    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0, 0, 0, 1};
     if (params) p = *params;
     if (p.precision < NSG_PREC_F32 || p.precision > NSG_PREC_U8) return NSG_EINVAL;
     if (p.init_random < 0 || p.init_random > L) return NSG_EINVAL;
+    if (p.warps_per_query != 0 && p.warps_per_query != 1 && p.warps_per_query != 2 && p.warps_per_query != 4)
+        return NSG_EINVAL;
     if (p.precision != NSG_PREC_F32 && !idx->lowp[p.precision]) return NSG_EINVAL;  // nsg_index_prepare first
     if (p.hash_slots > 0 && (p.hash_slots < 64 || (p.hash_slots & (p.hash_slots - 1)) || p.hash_slots > 65536))
         return NSG_EINVAL;
@@ -725,6 +727,7 @@ nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t n
     l.any_capped = nullptr;
     l.init_count = p.init_random;
     l.init_seed = p.init_seed;
+    l.warps_per_query = p.warps_per_query > 1 ? p.warps_per_query : 1;
     if (p.precision != NSG_PREC_F32) {
         l.precision = p.precision;
         l.lowp = idx->lowp[p.precision];
@@ -864,12 +867,16 @@ nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best = 1e30f, worst = 0.0f;
-        int bw = 0, bh = 0, tried = 0;
-        for (int w : {2, 4, 8})
+        int bw = 0, bh = 0, bq = 1, tried = 0;
+        const bool groups_ok = p->l.stop_model == nullptr;  // the stop kernels run one warp per query
+        for (int q : {1, 2, 4})
+            for (int w : {2, 4, 8})
             for (int h : {512, 1024, 2048}) {
+                if (w < q || (q > 1 && !groups_ok)) continue;
                 nsg::SearchLaunch t = p->l;
                 t.warps_per_cta = w;
                 t.hash_slots = h;
+                t.warps_per_query = q;
                 if (batched_run(t, st) || cudaStreamSynchronize(st) != cudaSuccess) continue;
                 cudaEventRecord(e0, st);
                 bool ok = true;
@@ -885,6 +892,7 @@ nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64
                     best = ms;
                     bw = w;
                     bh = h;
+                    bq = q;
                 }
             }
         cudaEventDestroy(e0);
@@ -892,6 +900,7 @@ nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64
         if (tried) {
             p->l.warps_per_cta = bw;
             p->l.hash_slots = bh;
+            p->l.warps_per_query = bq;
             p->info.best_ms = best;
             p->info.worst_ms = worst;
         }
@@ -899,6 +908,7 @@ nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64
     }
     p->info.warps_per_cta = p->l.warps_per_cta > 0 ? p->l.warps_per_cta : 4;
     p->info.hash_slots = p->l.hash_slots;
+    p->info.warps_per_query = p->l.warps_per_query;
     // capture "reset counter + search" once; a run replays it
     s = batched_run(p->l, st);  // sets kernel attributes outside the capture
     cudaError_t e = cudaStreamSynchronize(st);
@@ -941,7 +951,7 @@ nsg_status nsg_search_trace(const nsg_index *idx, const float *queries_dev, int6
                             const nsg_search_params *params, int32_t *ids_dev, float *feat_dev,
                             uint8_t *flag_dev, int32_t *steps_dev, int32_t cap, void *stream) {
     if (cap < 1 || (nq > 0 && (!feat_dev || !flag_dev || !steps_dev))) return NSG_EINVAL;
-    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0, 0, 0};
+    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0, 0, 0, 1};
     if (params) p = *params;
     p.stop_model = nullptr;  // traces record the fixed-L search
     nsg::SearchLaunch l;

@@ -22,6 +22,7 @@ struct SearchLaunch {
     int64_t nq;
     int k, L;
     int hash_slots, max_steps, warps_per_cta;
+    int warps_per_query = 1;  // 1, 2 or 4 warps share a query (search_group_kernel)
     int *ids;
     float *d2;
     int *n_expand, *n_dist, *status;

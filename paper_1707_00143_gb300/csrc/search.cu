@@ -1,6 +1,7 @@
 // search.cu -- Alg. 1 for a batch of queries (search on NSG, Section 3.5) and
 // the per-node search-and-collect of Alg. 2 (lines 5-8), one warp per unit.
 #include <algorithm>
+#include <type_traits>
 
 #include <cuda_fp16.h>
 
@@ -83,12 +84,87 @@ struct SearchArgs {
     int n;
 };
 
-// Alg. 1 per query.  P = PREC_F32: distances on the FP32 rows (the plain
-// form).  P = PREC_BF16 / PREC_FP8 / PREC_U8: traversal distances on the
-// low-precision copy; with `rerank` the L pool entries are then measured again
-// on the FP32 rows and the k smallest of those keys are returned.  The re-rank
-// list reuses the visited hash (no longer needed once the pool is final) when
-// it has room for k keys, else a list of its own (C = k).
+// The distance functor of precision P for one query (every lane loads its
+// share of the query), handed to f.  Returns whether the 8-bit map kept
+// every query value (always true for the other forms).
+template <int G, int V, int U, int P, class F>
+__device__ __forceinline__ bool with_dist(const SearchArgs &a, const float *qp, F &&f) {
+    if constexpr (P == PREC_F32) {
+        DistF32<G, V, U> dist{{}, a.base4, a.dp4};
+        dist.Q.load(qp, a.d, a.dp4);
+        f(dist);
+        return true;
+    } else if constexpr (P == PREC_U8) {
+        // an 8-bit row is a quarter of the FP32 row: G8 lanes of up to
+        // NSG_U8CHUNKS 16-byte chunks each, 32 / G8 rows per pass
+        constexpr int VG = V * G;  // FP32 float4 capacity of a lane group
+        constexpr int G8 = VG / (4 * NSG_U8CHUNKS) < 1 ? 1 : (VG / (4 * NSG_U8CHUNKS) > 32 ? 32 : VG / (4 * NSG_U8CHUNKS));
+        constexpr int VC = VG / (4 * G8);
+        // rows of 513..1024 values run with the default register budget:
+        // more of them in flight
+        constexpr int U8R = V == 8 ? NSG_U8ROWS_WIDE : (V > 8 ? 2 : NSG_U8ROWS);
+        DistU8<G8, VC, U8R> dist{{}, a.lowp, a.dc};
+        const bool qexact = dist.Q.load(qp, a.d, a.lo, a.scale);
+        f(dist);
+        return qexact;
+    } else {
+        constexpr int VC = (V * 4) / PrecEpc<P>::value > 0 ? (V * 4) / PrecEpc<P>::value : 1;
+        // rows in flight per group: a low-precision row costs VC*4 registers per lane
+        constexpr int UL = V == 8 ? NSG_UL_WIDE : (VC <= 1 ? NSG_UL1 : (VC == 2 ? NSG_UL2 : 2));
+        DistLp<P, G, VC, UL> dist{{}, a.lowp, a.dc};
+        dist.Q.load(qp, a.d, a.scale);
+        f(dist);
+        return true;
+    }
+}
+
+// After the traversal of query qi (one warp): with `rerank` the L pool
+// entries are measured again on the FP32 rows and the k smallest of those
+// keys are kept (the re-rank list reuses the visited hash, no longer needed,
+// when it has room for k keys, else a list of its own, C = k); then the
+// results and counters are written.
+template <int G, int V, int U, int P>
+__device__ __forceinline__ void finish_query(const SearchArgs &a, WarpSmem &s, const SearchOut &o, int64_t qi,
+                                             int kq, const float *qp, bool rerank) {
+    const unsigned lane = lane_id();
+    const uint64_t *res = s.pool;
+    int rsize = o.size;
+    if constexpr (P != PREC_F32) if (rerank) {
+        uint64_t *cl = a.C > 0 ? s.clist : reinterpret_cast<uint64_t *>(s.hash);
+        // the re-rank gathers all L pool rows at once: more rows in flight
+        // than the traversal for rows of 513..1024 values
+        constexpr int UR = V == 8 ? NSG_U_RERANK_WIDE : U;
+        DistF32<G, V, UR> exact{{}, a.base4, a.dp4};
+        exact.Q.load(qp, a.d, a.dp4);
+        int kept = 0;
+        for (int c0 = 0; c0 < o.size; c0 += a.W) {
+            const int mm = o.size - c0 < a.W ? o.size - c0 : a.W;
+            for (int t = lane; t < mm; t += 32) s.ids[t] = kid(s.pool[c0 + t]);
+            __syncwarp();
+            exact(s.ids, mm, s.keys);
+            warp_merge(cl, kq, kept, s.keys, mm, s.ck, s.cp, s.sk, s.sp);
+        }
+        res = cl;
+        rsize = kept;
+    }
+    for (int c = lane; c < a.k; c += 32) {  // row stride a.k; slots past this query's k padded
+        const bool has = c < rsize && c < kq;
+        uint64_t e = has ? res[c] : KEY_INF;
+        a.ids[qi * a.k + c] = has ? kid(e) : -1;
+        if (a.d2) a.d2[qi * a.k + c] = has ? kd2(e) : __int_as_float(0x7f800000);
+    }
+    if (lane == 0) {
+        if (a.n_expand) a.n_expand[qi] = o.n_expand;
+        if (a.n_dist) a.n_dist[qi] = o.n_dist;
+        if (a.status) a.status[qi] = o.capped ? -4 : 0;
+        if (o.capped && a.any_capped) atomicOr(a.any_capped, 1);
+    }
+    __syncwarp();
+}
+
+// Alg. 1 per query, one warp each.  P = PREC_F32: distances on the FP32 rows
+// (the plain form).  P = PREC_BF16 / PREC_FP8 / PREC_U8: traversal distances
+// on the low-precision copy, then the FP32 re-rank when asked for.
 template <int G, int V, int U, int P, bool STOP>
 __device__ __forceinline__ void search_body(const SearchArgs &a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -130,71 +206,55 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
         const InitRand ir{a.init_count < Lq ? a.init_count : Lq, a.init_seed, qi, a.n};
         const InitRand *initp = a.init_count > 0 ? &ir : nullptr;
         SearchOut o;
-        bool rerank = a.rerank == 1;
-        if constexpr (P == PREC_F32) {
-            DistF32<G, V, U> dist{{}, a.base4, a.dp4};
-            dist.Q.load(qp, a.d, a.dp4);
-            o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, Lq, s,
-                                                              (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
-                                                              csize, nullptr, 0, scp, nullptr, initp);
-        } else if constexpr (P == PREC_U8) {
-            // an 8-bit row is a quarter of the FP32 row: G8 lanes of up to
-            // NSG_U8CHUNKS 16-byte chunks each, 32 / G8 rows per pass
-            constexpr int VG = V * G;  // FP32 float4 capacity of a lane group
-            constexpr int G8 = VG / (4 * NSG_U8CHUNKS) < 1 ? 1 : (VG / (4 * NSG_U8CHUNKS) > 32 ? 32 : VG / (4 * NSG_U8CHUNKS));
-            constexpr int VC = VG / (4 * G8);
-            // rows of 513..1024 values run with the default register budget:
-            // more of them in flight
-            constexpr int U8R = V == 8 ? NSG_U8ROWS_WIDE : (V > 8 ? 2 : NSG_U8ROWS);
-            DistU8<G8, VC, U8R> dist{{}, a.lowp, a.dc};
-            const bool qexact = dist.Q.load(qp, a.d, a.lo, a.scale);
-            rerank = rerank || (a.rerank == 2 && !qexact);
-            o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, Lq, s,
-                                                              (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
-                                                              csize, nullptr, 0, scp, nullptr, initp);
-        } else {
-            constexpr int VC = (V * 4) / PrecEpc<P>::value > 0 ? (V * 4) / PrecEpc<P>::value : 1;
-            // rows in flight per group: a low-precision row costs VC*4 registers per lane
-            constexpr int UL = V == 8 ? NSG_UL_WIDE : (VC <= 1 ? NSG_UL1 : (VC == 2 ? NSG_UL2 : 2));
-            DistLp<P, G, VC, UL> dist{{}, a.lowp, a.dc};
-            dist.Q.load(qp, a.d, a.scale);
-            o = warp_alg1<false, false, decltype(dist), STOP>(dist, GraphRef{a.adj, a.width}, a.start, Lq, s,
-                                                              (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
-                                                              csize, nullptr, 0, scp, nullptr, initp);
-        }
-        const uint64_t *res = s.pool;
-        int rsize = o.size;
-        if constexpr (P != PREC_F32) if (rerank) {
-            uint64_t *cl = a.C > 0 ? s.clist : reinterpret_cast<uint64_t *>(s.hash);
-            // the re-rank gathers all L pool rows at once: more rows in flight
-            // than the traversal for rows of 513..1024 values
-            constexpr int UR = V == 8 ? NSG_U_RERANK_WIDE : U;
-            DistF32<G, V, UR> exact{{}, a.base4, a.dp4};
-            exact.Q.load(qp, a.d, a.dp4);
-            int kept = 0;
-            for (int c0 = 0; c0 < o.size; c0 += a.W) {
-                const int mm = o.size - c0 < a.W ? o.size - c0 : a.W;
-                for (int t = lane; t < mm; t += 32) s.ids[t] = kid(s.pool[c0 + t]);
-                __syncwarp();
-                exact(s.ids, mm, s.keys);
-                warp_merge(cl, kq, kept, s.keys, mm, s.ck, s.cp, s.sk, s.sp);
-            }
-            res = cl;
-            rsize = kept;
-        }
-        for (int c = lane; c < a.k; c += 32) {  // row stride a.k; slots past this query's k padded
-            const bool has = c < rsize && c < kq;
-            uint64_t e = has ? res[c] : KEY_INF;
-            a.ids[qi * a.k + c] = has ? kid(e) : -1;
-            if (a.d2) a.d2[qi * a.k + c] = has ? kd2(e) : __int_as_float(0x7f800000);
-        }
-        if (lane == 0) {
-            if (a.n_expand) a.n_expand[qi] = o.n_expand;
-            if (a.n_dist) a.n_dist[qi] = o.n_dist;
-            if (a.status) a.status[qi] = o.capped ? -4 : 0;
-            if (o.capped && a.any_capped) atomicOr(a.any_capped, 1);
-        }
-        __syncwarp();
+        const bool qexact = with_dist<G, V, U, P>(a, qp, [&](const auto &dist) {
+            o = warp_alg1<false, false, std::decay_t<decltype(dist)>, STOP>(
+                dist, GraphRef{a.adj, a.width}, a.start, Lq, s, (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
+                csize, nullptr, 0, scp, nullptr, initp);
+        });
+        const bool rerank = a.rerank == 1 || (P == PREC_U8 && a.rerank == 2 && !qexact);
+        finish_query<G, V, U, P>(a, s, o, qi, kq, qp, rerank);
+    }
+}
+
+// Alg. 1 per query by a group of WPQ warps that share the query's pool and
+// visited set (group_alg1): WPQ times the rows in flight per expansion, the
+// same steps and results.  Group g of a block uses named barrier 1 + g.
+struct GroupCtl {
+    int64_t t;  // the group's query (drawn by the leader)
+    int m, done;
+};
+
+template <int G, int V, int U, int P, int WPQ>
+__device__ __forceinline__ void search_group_body(const SearchArgs &a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const int g = warp / WPQ, w = warp % WPQ, gpb = wpb / WPQ;
+    const unsigned lane = lane_id();
+    const size_t wbytes = warp_smem_bytes(a.L, a.W, a.C, a.H);
+    WarpSmem s = carve_warp_smem(smem + g * wbytes, a.L, a.W, a.C, a.H);
+    volatile GroupCtl *ctl = reinterpret_cast<volatile GroupCtl *>(smem + gpb * wbytes) + g;
+    const int bar_id = 1 + g;
+    const int64_t stride = (int64_t)gridDim.x * gpb;
+    int64_t tstat = (int64_t)blockIdx.x * gpb + g;
+    for (;;) {
+        if (w == 0 && lane == 0) ctl->t = a.work != nullptr ? (int64_t)atomicAdd(a.work, 1) : tstat;
+        tstat += stride;
+        group_bar(bar_id, 32 * WPQ);
+        const int64_t t = ctl->t;
+        if (t >= a.nq) break;  // the same value in every warp of the group
+        const int64_t qi = a.order != nullptr ? a.order[t] : t;
+        const int kq = a.kv != nullptr ? min(max(a.kv[qi], 1), a.k) : a.k;
+        const int Lq = a.Lv != nullptr ? max(min(a.Lv[qi], a.L), kq) : a.L;
+        const float *qp = a.queries + qi * a.d;
+        const InitRand ir{a.init_count < Lq ? a.init_count : Lq, a.init_seed, qi, a.n};
+        const InitRand *initp = a.init_count > 0 ? &ir : nullptr;
+        SearchOut o;
+        const bool qexact = with_dist<G, V, U, P>(a, qp, [&](const auto &dist) {
+            o = group_alg1<WPQ>(dist, GraphRef{a.adj, a.width}, a.start, Lq, s, (uint32_t)a.H - 1, a.hshift,
+                                a.max_steps, w, bar_id, ctl, initp);
+        });
+        const bool rerank = a.rerank == 1 || (P == PREC_U8 && a.rerank == 2 && !qexact);
+        if (w == 0) finish_query<G, V, U, P>(a, s, o, qi, kq, qp, rerank);
     }
 }
 
@@ -204,7 +264,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
 // also carry the FP32 re-rank) take ~112 registers and the plain one 70.
 // Wider rows (V >= 8) keep the compiler's default budget (~98), since 64 would
 // spill.  The learned-stop / trace kernels carry the feature and MLP code and
-// are held to 3 blocks per SM.
+// are held to 3 blocks per SM (rows up to 512 values) or left free (wider).
 template <int G, int V, int U, int P>
 __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a) {
     search_body<G, V, U, P, false>(a);
@@ -217,13 +277,34 @@ template <int G, int V, int U, int P>
 __global__ void __launch_bounds__(256, NSG_STOP_MINB) search_stop_kernel(SearchArgs a) {
     search_body<G, V, U, P, true>(a);
 }
-
-// Kernel for precision P at the dispatch shape G, V, U.
 template <int G, int V, int U, int P>
-static void (*search_entry(bool stop))(SearchArgs) {
-    if (stop) return search_stop_kernel<G, V, U, P>;
-    if constexpr (V <= 4) return search_kernel<G, V, U, P>;
-    else return search_wide_kernel<G, V, U, P>;
+__global__ void __launch_bounds__(256) search_stop_wide_kernel(SearchArgs a) {
+    search_body<G, V, U, P, true>(a);
+}
+template <int G, int V, int U, int P, int WPQ>
+__global__ void __launch_bounds__(256, 4) search_group_kernel(SearchArgs a) {
+    search_group_body<G, V, U, P, WPQ>(a);
+}
+template <int G, int V, int U, int P, int WPQ>
+__global__ void __launch_bounds__(256) search_group_wide_kernel(SearchArgs a) {
+    search_group_body<G, V, U, P, WPQ>(a);
+}
+
+// Kernel for precision P at the dispatch shape G, V, U (wpq warps per query;
+// the learned-stop / trace kernels run one warp per query).
+template <int G, int V, int U, int P>
+static void (*search_entry(bool stop, int wpq))(SearchArgs) {
+    if constexpr (V <= 4) {
+        if (stop) return search_stop_kernel<G, V, U, P>;
+        if (wpq == 2) return search_group_kernel<G, V, U, P, 2>;
+        if (wpq == 4) return search_group_kernel<G, V, U, P, 4>;
+        return search_kernel<G, V, U, P>;
+    } else {
+        if (stop) return search_stop_wide_kernel<G, V, U, P>;
+        if (wpq == 2) return search_group_wide_kernel<G, V, U, P, 2>;
+        if (wpq == 4) return search_group_wide_kernel<G, V, U, P, 4>;
+        return search_wide_kernel<G, V, U, P>;
+    }
 }
 
 struct CollectArgs {
@@ -284,10 +365,12 @@ __global__ void __launch_bounds__(256) collect_kernel(CollectArgs a) {
 
 template <typename K>
 static cudaError_t config(K kernel, size_t smem_per_warp, int want_wpb, int64_t units, int *grid,
-                          int *wpb, size_t *smem, size_t smem_per_cta = 0) {
+                          int *wpb, size_t *smem, size_t smem_per_cta = 0, int step = 1) {
+    // warps per block: a multiple of `step` (the warps of one query group)
     size_t cap = smem_optin();
     int w = want_wpb > 0 ? want_wpb : 4;
-    while (w > 1 && smem_per_warp * w + smem_per_cta > cap) --w;
+    w = w < step ? step : w / step * step;
+    while (w > step && smem_per_warp * w + smem_per_cta > cap) w -= step;
     if (smem_per_warp * w + smem_per_cta > cap) return cudaErrorInvalidConfiguration;
     *smem = smem_per_warp * w + smem_per_cta;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
@@ -350,15 +433,19 @@ cudaError_t launch_search(const SearchLaunch &l, cudaStream_t st) {
     size_t per_warp = warp_smem_bytes(a.L, a.W, a.C, a.H);
     const size_t per_cta = l.stop_model ? ((sizeof(StopMLP) + 15) & ~size_t(15)) : 0;
     cudaError_t err = cudaSuccess;
+    const bool stop = l.stop_model != nullptr || l.trace_feat != nullptr;
+    // warps per query: 1, 2 or 4 (the learned-stop / trace kernels use 1)
+    const int wpq = stop ? 1 : (l.warps_per_query == 2 || l.warps_per_query == 4 ? l.warps_per_query : 1);
+    // a group's region and its control word, spread over its warps
+    if (wpq > 1) per_warp = ((per_warp + 32) / wpq + 15) & ~size_t(15);
     NSG_DISPATCH_DP4(a.dp4, {
-        const bool stop = l.stop_model != nullptr || l.trace_feat != nullptr;
-        auto kern = l.precision == PREC_BF16  ? search_entry<G_, V_, U_, PREC_BF16>(stop)
-                    : l.precision == PREC_FP8 ? search_entry<G_, V_, U_, PREC_FP8>(stop)
-                    : l.precision == PREC_U8  ? search_entry<G_, V_, U_, PREC_U8>(stop)
-                                              : search_entry<G_, V_, U_, PREC_F32>(stop);
+        auto kern = l.precision == PREC_BF16  ? search_entry<G_, V_, U_, PREC_BF16>(stop, wpq)
+                    : l.precision == PREC_FP8 ? search_entry<G_, V_, U_, PREC_FP8>(stop, wpq)
+                    : l.precision == PREC_U8  ? search_entry<G_, V_, U_, PREC_U8>(stop, wpq)
+                                              : search_entry<G_, V_, U_, PREC_F32>(stop, wpq);
         int grid, wpb;
         size_t smem;
-        err = config(kern, per_warp, l.warps_per_cta, l.nq, &grid, &wpb, &smem, per_cta);
+        err = config(kern, per_warp, l.warps_per_cta, l.nq * wpq, &grid, &wpb, &smem, per_cta, wpq);
         if (err == cudaSuccess) {
             kern<<<grid, wpb * 32, smem, st>>>(a);
             err = cudaGetLastError();

@@ -176,22 +176,61 @@ __device__ __forceinline__ uint64_t splitmix64_dev(uint64_t x) {
     return z ^ (z >> 31);
 }
 
-// `dist(ids, m, keys)` writes keys[c] = (d2(query, row ids[c]), ids[c]) for c < m.
-// STOP: compile the learned-stop / trace hooks (stop must then be non-null).
-template <bool COLLECT, bool COHERENT, class D, bool STOP = false>
-__device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, WarpSmem &s, uint32_t hmask,
-                               int hshift, int max_steps, int excl, int C, int &csize, int *xlog = nullptr,
-                               int xcap = 0, const StopCtx *stop = nullptr, uint64_t *xthr = nullptr,
-                               const InitRand *init = nullptr) {
+// First unchecked pool entry at or after `cursor` (entries before it are all
+// checked), or -1.  Warp-wide.
+__device__ __forceinline__ int first_unchecked(const uint64_t *pool, int size, int cursor) {
     const unsigned lane = lane_id();
-    SearchOut o;
-    o.size = 0;
-    o.n_expand = 0;
-    o.n_dist = 0;
-    o.capped = false;
-    o.stopped = false;
-    int since_change = 0, last_m = 0;
-    bool last_changed = true;
+    for (int b = cursor; b < size; b += 32) {
+        const int j = b + (int)lane;
+        const bool unchecked = j < size && !(pool[j] & CHK);
+        const unsigned bal = __ballot_sync(NSG_FULL, unchecked);
+        if (bal) return b + __ffs(bal) - 1;
+    }
+    return -1;
+}
+
+// Reads node u's adjacency row and keeps the neighbours the visited set has
+// not seen, in row order, in s.ids; returns their count.  Warp-wide.  The
+// first 128 slots are loaded before any visit (the visited-set updates would
+// otherwise order each 32-slot load after the previous chunk's), so a row
+// costs one global round trip.
+template <bool COHERENT>
+__device__ __forceinline__ int gather_row(GraphRef g, int u, WarpSmem &s, uint32_t hmask, int hshift) {
+    const unsigned lane = lane_id();
+    const int *row = g.adj + (int64_t)u * g.width;
+    int m = 0;
+    int vr[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int slot = c * 32 + (int)lane;
+        vr[c] = slot < g.width ? load_adj<COHERENT>(row + slot) : -1;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (c * 32 >= g.width) break;
+        const bool fresh = vr[c] >= 0 && visit(s.hash, hmask, hshift, vr[c]);
+        const unsigned bal = __ballot_sync(NSG_FULL, fresh);
+        if (fresh) s.ids[m + __popc(bal & lanemask_lt())] = vr[c];
+        m += __popc(bal);
+    }
+    for (int b = 128; b < g.width; b += 32) {  // rows wider than 128
+        const int slot = b + (int)lane;
+        const int v = slot < g.width ? load_adj<COHERENT>(row + slot) : -1;
+        const bool fresh = v >= 0 && visit(s.hash, hmask, hshift, v);
+        const unsigned bal = __ballot_sync(NSG_FULL, fresh);
+        if (fresh) s.ids[m + __popc(bal & lanemask_lt())] = v;
+        m += __popc(bal);
+    }
+    __syncwarp();
+    return m;
+}
+
+// The initial pool: the start node, or the set of `init->count` seeded
+// random nodes.  Warp-wide; clears the visited set first.
+template <class D>
+__device__ __forceinline__ void init_pool(const D &dist, int start, int L, WarpSmem &s, uint32_t hmask, int hshift,
+                                          const InitRand *init, SearchOut &o) {
+    const unsigned lane = lane_id();
     hash_clear(s.hash, (int)hmask + 1);
     if (init != nullptr && init->count > 0) {
         // the pool starts as the set of the drawn nodes, 32 draws at a time
@@ -224,20 +263,105 @@ __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, Warp
         if (lane == 0) s.pool[0] = s.keys[0];
         __syncwarp();
         o.size = 1;
-        if (COLLECT) collect_merge(s, 1, excl, C, csize);
     }
-    int cursor = 0;
+}
+
+// Barrier over the first `nthreads` threads that reach named barrier `id`.
+__device__ __forceinline__ void group_bar(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Alg. 1 for one query by a group of WPQ warps sharing the pool and visited
+// set in shared memory.  Per expansion the leader warp (w == 0) finds the
+// node, reads its row and filters it through the visited set; after barrier
+// A every warp measures a contiguous slice of the new neighbours; after
+// barrier B the leader merges them into the pool.  The steps, keys and merges
+// are those of warp_alg1 (one warp), so are the results; the group has WPQ
+// times the rows in flight.  Every warp of the group runs the same sequence
+// of barriers: the leader's decisions (rows to measure, done) are read from
+// `ctl` after barrier A.  The returned counters are the leader's.
+template <int WPQ, class D, class Ctl>
+__device__ SearchOut group_alg1(const D &dist, GraphRef g, int start, int L, WarpSmem &s, uint32_t hmask,
+                                int hshift, int max_steps, int w, int bar_id, volatile Ctl *ctl,
+                                const InitRand *init) {
+    const unsigned lane = lane_id();
+    SearchOut o;
+    o.size = 0;
+    o.n_expand = 0;
+    o.n_dist = 0;
+    o.capped = false;
+    o.stopped = false;
+    if (w == 0) init_pool(dist, start, L, s, hmask, hshift, init, o);
+    int cursor = 0, i = -1;
     for (;;) {
-        int i = -1;
-        for (int b = cursor; b < o.size; b += 32) {
-            int j = b + (int)lane;
-            bool unchecked = j < o.size && !(s.pool[j] & CHK);
-            unsigned bal = __ballot_sync(NSG_FULL, unchecked);
-            if (bal) {
-                i = b + __ffs(bal) - 1;
-                break;
+        if (w == 0) {
+            i = first_unchecked(s.pool, o.size, cursor);
+            int m = 0, done = 0;
+            if (i < 0) {
+                done = 1;
+            } else if (o.n_expand >= max_steps) {
+                o.capped = true;
+                done = 1;
+            } else {
+                o.n_expand++;
+                const uint64_t e = s.pool[i];
+                __syncwarp();
+                if (lane == 0) s.pool[i] = e | CHK;
+                m = gather_row<false>(g, kid(e), s, hmask, hshift);
+#if NSG_PF_ROWS
+                if (m > 0) dist.prefetch(s.ids, m);
+#endif
+            }
+            if (lane == 0) {
+                ctl->m = m;
+                ctl->done = done;
+            }
+            __syncwarp();
+        }
+        group_bar(bar_id, 32 * WPQ);  // A: the row's new neighbours are in s.ids
+        const int m = ctl->m;
+        if (ctl->done) break;
+        if (m > 0) {
+            const int per = (m + WPQ - 1) / WPQ;
+            const int lo = w * per;
+            const int cnt = m - lo < per ? m - lo : per;
+            if (cnt > 0) dist(s.ids + lo, cnt, s.keys + lo);
+        }
+        group_bar(bar_id, 32 * WPQ);  // B: their keys are in s.keys
+        if (w == 0) {
+            if (m > 0) {
+                o.n_dist += m;
+                const int lo = warp_merge(s.pool, L, o.size, s.keys, m, s.ck, s.cp, s.sk, s.sp);
+                cursor = min(i + 1, lo);
+            } else {
+                cursor = i + 1;
             }
         }
+    }
+    return o;
+}
+
+// `dist(ids, m, keys)` writes keys[c] = (d2(query, row ids[c]), ids[c]) for c < m.
+// STOP: compile the learned-stop / trace hooks (stop must then be non-null).
+template <bool COLLECT, bool COHERENT, class D, bool STOP = false>
+__device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, WarpSmem &s, uint32_t hmask,
+                               int hshift, int max_steps, int excl, int C, int &csize, int *xlog = nullptr,
+                               int xcap = 0, const StopCtx *stop = nullptr, uint64_t *xthr = nullptr,
+                               const InitRand *init = nullptr) {
+    const unsigned lane = lane_id();
+    SearchOut o;
+    o.size = 0;
+    o.n_expand = 0;
+    o.n_dist = 0;
+    o.capped = false;
+    o.stopped = false;
+    int since_change = 0, last_m = 0;
+    bool last_changed = true;
+    init_pool(dist, start, L, s, hmask, hshift, init, o);
+    if (COLLECT && (init == nullptr || init->count <= 0)) collect_merge(s, 1, excl, C, csize);
+    int cursor = 0;
+    for (;;) {
+        const int i = first_unchecked(s.pool, o.size, cursor);
         if (i < 0) break;
         if (o.n_expand >= max_steps) {
             o.capped = true;
@@ -284,34 +408,7 @@ __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, Warp
             // only below the L-th key (anything, while the pool is not full)
             if (xthr != nullptr) xthr[o.n_expand - 1] = o.size < L ? KEY_INF : kval(s.pool[L - 1]);
         }
-        const int *row = g.adj + (int64_t)u * g.width;
-        int m = 0;
-        // the first 128 slots of the row are loaded before any visit (the
-        // visited-set updates would otherwise order each 32-slot load after
-        // the previous chunk's), so a row costs one global round trip
-        int vr[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int slot = c * 32 + (int)lane;
-            vr[c] = slot < g.width ? load_adj<COHERENT>(row + slot) : -1;
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            if (c * 32 >= g.width) break;
-            const bool fresh = vr[c] >= 0 && visit(s.hash, hmask, hshift, vr[c]);
-            const unsigned bal = __ballot_sync(NSG_FULL, fresh);
-            if (fresh) s.ids[m + __popc(bal & lanemask_lt())] = vr[c];
-            m += __popc(bal);
-        }
-        for (int b = 128; b < g.width; b += 32) {  // rows wider than 128
-            const int slot = b + (int)lane;
-            const int v = slot < g.width ? load_adj<COHERENT>(row + slot) : -1;
-            const bool fresh = v >= 0 && visit(s.hash, hmask, hshift, v);
-            const unsigned bal = __ballot_sync(NSG_FULL, fresh);
-            if (fresh) s.ids[m + __popc(bal & lanemask_lt())] = v;
-            m += __popc(bal);
-        }
-        __syncwarp();
+        const int m = gather_row<COHERENT>(g, u, s, hmask, hshift);
         last_m = m;
 #if NSG_PF_ROWS
         if (m > 0) dist.prefetch(s.ids, m);
