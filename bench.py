@@ -168,10 +168,13 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-# ncu DRAM traffic of the search kernel per query on this workload, keyed by
-# the hash of the kernel sources it was measured on (see profiles/).  A source
-# change invalidates it and `traffic` becomes null until re-measured.
-NCU_TRAFFIC = {}
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# search launch, per query, keyed by (kernel source hash, workload, form, L):
+# profiles/search_kernel_u8_sift.md has the capture.  A source change changes
+# the hash, and `traffic` is null until re-measured.
+NCU_TRAFFIC = {
+    ("195177e4b30fa3eb", "sift", "u8", 150): (1_668_171_264 + 10_440_960) / 10_000,
+}
 
 
 def cpu_serial_scan(base, q, budget_s=10.0):
@@ -445,7 +448,7 @@ def main():
     peak, peak_kind = peaks()
     achieved = bytes_launch / (ms_step / 1e3) / 1e9
     src = kernel_source_hash()
-    tr = NCU_TRAFFIC.get((src, chosen_form, L))
+    tr = NCU_TRAFFIC.get((src, args.workload, chosen_form, L))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": (tr * nq if tr else None),
                 "peak_kind": peak_kind, "kernel": f"search_kernel ({chosen_form})",
