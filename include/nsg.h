@@ -7,7 +7,7 @@
  *  - Distances are SQUARED l2 (Section 2 defines delta as the l2 distance;
  *    the method only ever compares distances, so squaring changes nothing).
  *  - "Key order" is (squared distance, id) ascending.  It is the paper's
- *    "ascending order of the distance" (Alg. 1, Alg. 2 line 8) with the
+ *    "ascending order of the distance" (Alg. 1, and Alg. 2's candidate sort) with the
  *    lower-index tie rule of the MRNG definition (Section 3.3) applied to
  *    every tie.
  *  - Pointers named *_dev are device pointers (cudaMalloc / torch CUDA
@@ -105,6 +105,9 @@ typedef struct {
     int64_t n_fixup_searches; /* fix-ups whose speculative search was stale and ran again */
     int32_t has_u8;        /* 8-bit copy: 0 none, 1 lossy, 2 every value and distance exact */
     float u8_lo, u8_scale; /* x_u8 = clamp(rint((x - u8_lo) * u8_scale), 0, 255) */
+    int64_t prune_examined; /* candidates the MRNG edge selection examined over all nodes
+                               (0 when not built here): per node, every candidate up to the
+                               one that filled the row (R kept) or all of them */
 } nsg_index_info_t;
 
 /* Human-readable name of a status code (static string). */
@@ -133,14 +136,14 @@ nsg_status nsg_knn_query(const float *base_dev, int64_t n, int32_t d, const floa
                          int64_t nq, int32_t k, int32_t *ids_dev, float *d2_dev, void *stream);
 
 /* ---------------------------------------------------------------------------
- * A2. Centroid (Alg. 2 line 1): c_j = (sum_i x_ij) / n, summed in FP64.
+ * A2. Centroid (Alg. 2, first step): c_j = (sum_i x_ij) / n, summed in FP64.
  *   centroid_dev [d] f64 out.
  * ------------------------------------------------------------------------- */
 nsg_status nsg_centroid(const float *base_dev, int64_t n, int32_t d, double *centroid_dev,
                         void *stream);
 
 /* ---------------------------------------------------------------------------
- * A3. Navigating node (Alg. 2 lines 2-3; Section 3.4 step ii): Alg. 1 on the
+ * A3. Navigating node (Alg. 2; Section 3.4 step ii): Alg. 1 on the
  *   kNN graph from `start`, query = centroid, pool L; the navigating node is
  *   the first pool entry.  Distances to the centroid are FP64, summed over j
  *   in order without FMA contraction.  knn_ids_dev [n][K].
@@ -169,7 +172,7 @@ nsg_status nsg_navigate_noalloc(const float *base_dev, int64_t n, int32_t d, con
                                 int32_t *nav_host, void *stream);
 
 /* ---------------------------------------------------------------------------
- * A5. Search-and-collect (Alg. 2 lines 5-8; Section 3.4 step iii; Fig. 4) for
+ * A5. Search-and-collect (Alg. 2; Section 3.4 step iii; Fig. 4) for
  *   nodes v0 .. v0+nv-1: Alg. 1 on the kNN graph from `nav` with query x_v
  *   and pool L; every node whose distance was computed, plus v's K kNN
  *   neighbours, minus v itself, sorted by key and cut to the C smallest.
@@ -183,7 +186,7 @@ nsg_status nsg_collect(const float *base_dev, int64_t n, int32_t d, const int32_
                        int32_t *status_dev, void *stream);
 
 /* ---------------------------------------------------------------------------
- * A6. MRNG edge selection (Alg. 2 lines 9-20; Def. MRNG and Section 3.3) for
+ * A6. MRNG edge selection (Alg. 2; Def. MRNG and Section 3.3) for
  *   nodes v0 .. v0+nv-1 over their sorted candidates: the first candidate is
  *   kept; a later candidate p is dropped when some kept r has
  *   d2(p, r) < d2(p, v); stop at R kept.  Inputs as written by nsg_collect.
@@ -194,7 +197,7 @@ nsg_status nsg_prune(const float *base_dev, int64_t n, int32_t d, const int32_t 
                      int64_t v0, int64_t nv, int32_t *adj_dev, int32_t *deg_dev, void *stream);
 
 /* ---------------------------------------------------------------------------
- * A7. Connectivity (Alg. 2 lines 21-28; Section 3.4 step iv): reach from
+ * A7. Connectivity (Alg. 2; Section 3.4 step iv): reach from
  *   `nav` (BFS; the same reached set as the paper's DFS tree).  While a node
  *   is unreached: u = smallest unreached id; Alg. 1 on the current graph from
  *   nav with query x_u and pool L; the first result (key order) whose

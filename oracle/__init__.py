@@ -164,12 +164,12 @@ def splitmix64(x: int) -> int:
 
 
 def start_node(seed: int, n: int) -> int:
-    """Random start node of Alg. 2 line 2: splitmix64(seed) mod n."""
+    """Random start node of Alg. 2: splitmix64(seed) mod n (reading R5)."""
     return splitmix64(seed) % n
 
 
 def centroid(base):
-    """Alg. 2 line 1: mean row in double."""
+    """Centroid step of Alg. 2: mean row in double."""
     base = _f32(base)
     n, d = base.shape
     c = np.empty(d, np.float64)
@@ -178,7 +178,7 @@ def centroid(base):
 
 
 def navigate(knn, base, c, r, L):
-    """Alg. 2 lines 2-3: navigating node from start r toward centroid c."""
+    """Navigating-node step of Alg. 2: from start r toward centroid c."""
     knn, base = _i32(knn), _f32(base)
     c = np.ascontiguousarray(c, np.float64)
     nav = C.c_int32(0)
@@ -188,7 +188,7 @@ def navigate(knn, base, c, r, L):
 
 
 def collect(knn, base, nav, v, L, Cap):
-    """Alg. 2 lines 5-8 for node v: (ids, dists, count, n_expand, n_dist)."""
+    """Search-and-collect step of Alg. 2 for node v: (ids, dists, count, n_expand, n_dist)."""
     knn, base = _i32(knn), _f32(base)
     ids = np.empty(Cap, np.int32)
     dist = np.empty(Cap, np.float32)
@@ -201,7 +201,7 @@ def collect(knn, base, nav, v, L, Cap):
 
 
 def prune(base, cand_ids, cand_dist, R):
-    """Alg. 2 lines 9-20: MRNG edge selection; returns (row [R] -1 padded, deg)."""
+    """MRNG edge selection of Alg. 2; returns (row [R] -1 padded, deg)."""
     base = _f32(base)
     ci, cd = _i32(cand_ids), _f32(cand_dist)
     ncand = int(np.sum(ci >= 0)) if len(ci) else 0
@@ -213,7 +213,7 @@ def prune(base, cand_ids, cand_dist, R):
 
 
 def select_all(knn, base, nav, L, R, Cap, nthreads=None):
-    """Alg. 2 lines 4-20 for every node (before the connectivity pass)."""
+    """Alg. 2's per-node collect and select for every node (before the connectivity pass)."""
     knn, base = _i32(knn), _f32(base)
     n, d = base.shape
     adj = np.empty((n, R), np.int32)
@@ -224,7 +224,7 @@ def select_all(knn, base, nav, L, R, Cap, nthreads=None):
 
 
 def connect(adj, deg, base, nav, L, added_cap=1 << 16):
-    """Alg. 2 lines 21-28 on copies of adj/deg; returns (adj, deg, added [m][2])."""
+    """Connectivity step of Alg. 2 on copies of adj/deg; returns (adj, deg, added [m][2])."""
     adj = np.array(adj, dtype=np.int32, copy=True, order="C")
     deg = np.array(deg, dtype=np.int32, copy=True, order="C")
     base = _f32(base)

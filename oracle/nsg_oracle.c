@@ -527,7 +527,7 @@ uint64_t orc_splitmix64(uint64_t x) {
     return z ^ (z >> 31);
 }
 
-/* Alg. 2 line 1: the centroid, summed in double over i in order, then / n. */
+/* Alg. 2, centroid step: the centroid, summed in double over i in order, then / n. */
 int orc_centroid(const float *base, int64_t n, int32_t d, double *c) {
     if (!base || !c || n < 1 || d < 1) return ORC_EINVAL;
     for (int32_t j = 0; j < d; ++j) {
@@ -538,7 +538,7 @@ int orc_centroid(const float *base, int64_t n, int32_t d, double *c) {
     return ORC_OK;
 }
 
-/* Alg. 2 lines 2-3: Alg. 1 on the kNN graph from r toward the centroid;
+/* Alg. 2, navigating-node step: Alg. 1 on the kNN graph from r toward the centroid;
  * the navigating node is the nearest pool entry. */
 static int32_t navigate(const graph *knn, const float *base, int64_t n, int32_t d,
                         const double *c, int32_t r, int32_t l) {
@@ -567,7 +567,7 @@ int orc_navigate_lazy(orc_lazy_knn *knn, const double *c, int32_t r, int32_t l, 
     return ORC_OK;
 }
 
-/* Alg. 2 lines 5-8 (reading R3): candidates of node v, sorted, cut to C.
+/* Alg. 2, search-and-collect step (reading R3): candidates of node v, sorted, cut to C.
  * Returns the count written to cand_ids / cand_dist. */
 static int32_t collect(const graph *knn, const int32_t *knn_row_v, int32_t K, const float *base,
                        int64_t n, int32_t d, int32_t nav, int32_t v, int32_t l, int32_t C,
@@ -606,7 +606,7 @@ static int32_t collect(const graph *knn, const int32_t *knn_row_v, int32_t K, co
     return cnt;
 }
 
-/* Alg. 2 lines 9-20 (reading R4): MRNG edge selection over sorted candidates.
+/* Alg. 2, edge-selection loop (reading R4): MRNG edge selection over sorted candidates.
  * Writes up to R ids to out (-1 padded); returns the kept count. */
 static int32_t mrng_select(const float *base, int32_t d, const int32_t *cand_ids,
                            const float *cand_dist, int32_t ncand, int32_t R, int32_t *out) {
@@ -678,7 +678,7 @@ static void mark_reachable(const int32_t *adj, const int32_t *deg, int32_t R, in
     }
 }
 
-/* Alg. 2 lines 21-28 (reading R7).  adj/deg are updated in place. */
+/* Alg. 2, connectivity step (reading R7).  adj/deg are updated in place. */
 int orc_connect(int32_t *adj, int32_t *deg, int64_t n, int32_t R, const float *base, int32_t d,
                 int32_t nav, int32_t l, int32_t *n_added, int32_t *added, int32_t added_cap) {
     if (!adj || !deg || !base || nav < 0 || nav >= n) return ORC_EINVAL;
@@ -745,7 +745,7 @@ static void build_unit(void *p, int64_t v) {
     free(dist);
 }
 
-/* Alg. 2 lines 4-20 for every node, given the kNN graph and navigating node. */
+/* Alg. 2's per-node collect and select for every node, given the kNN graph and navigating node. */
 int orc_select_all(const int32_t *knn, int32_t K, const float *base, int64_t n, int32_t d,
                    int32_t nav, int32_t l, int32_t R, int32_t C, int32_t nthreads, int32_t *adj,
                    int32_t *deg) {

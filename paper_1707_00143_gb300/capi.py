@@ -53,7 +53,7 @@ class IndexInfo(C.Structure):
                 ("fp8_scale", C.c_float), ("ms_knn", C.c_float), ("ms_centroid_nav", C.c_float),
                 ("ms_collect", C.c_float), ("ms_prune", C.c_float), ("ms_connect", C.c_float),
                 ("ms_total", C.c_float), ("n_fixup_searches", C.c_int64), ("has_u8", C.c_int32),
-                ("u8_lo", C.c_float), ("u8_scale", C.c_float)]
+                ("u8_lo", C.c_float), ("u8_scale", C.c_float), ("prune_examined", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

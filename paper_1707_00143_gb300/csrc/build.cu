@@ -1,6 +1,6 @@
-// build.cu -- Alg. 2 kernels other than the per-node search: centroid (line 1),
-// navigating node (lines 2-3), MRNG edge selection (lines 9-20), reachability
-// BFS helpers of the connectivity pass (lines 21-28, see connect.cu); plus the
+// build.cu -- Alg. 2 kernels other than the per-node search: centroid,
+// navigating node, MRNG edge selection, reachability BFS helpers of the
+// connectivity pass (the pass itself is in connect.cu); plus the
 // precision count (Eq. 1) and a row-padding copy.
 #include <climits>
 
@@ -22,7 +22,7 @@ __device__ __forceinline__ T ld_volatile(const T *p) {
 }
 
 // ---------------------------------------------------------------------------
-// Centroid (Alg. 2 line 1): block b sums rows [b*rows, (b+1)*rows) of every
+// Centroid (Alg. 2, first step): block b sums rows [b*rows, (b+1)*rows) of every
 // column in FP64 (row order), then one pass adds the block sums in block order
 // and divides by n.  On integer data every partial sum is exact.
 // ---------------------------------------------------------------------------
@@ -57,7 +57,7 @@ cudaError_t launch_centroid(const float *base, int64_t n, int d, double *partial
 }
 
 // ---------------------------------------------------------------------------
-// Navigating node (Alg. 2 lines 2-3): Alg. 1 on the kNN graph from `start`
+// Navigating node (Alg. 2; Section 3.4 ii): Alg. 1 on the kNN graph from `start`
 // toward the centroid, one warp.  Distances are FP64 sums over j in order with
 // explicitly rounded operations (no FMA), so they do not depend on the
 // compiler.  Lanes compute the distances of the new neighbours; lane 0 keeps
@@ -176,7 +176,7 @@ cudaError_t launch_navigate(const float *base, int64_t n, int d, const int *knn,
 }
 
 // ---------------------------------------------------------------------------
-// MRNG edge selection (Alg. 2 lines 9-20), one warp per node.  Candidates are
+// MRNG edge selection (Alg. 2; Section 3.3), one warp per node.  Candidates are
 // already sorted by key; the first is kept; a later candidate p is occluded
 // when d2(p, r) < d2(p, v) for a kept r (r in the open lune of vp); stop at R.
 // The warp holds p's row; G-lane groups compute d2(p, r) for the kept rows.
@@ -190,6 +190,7 @@ struct PruneArgs {
     int C, R, Wr;
     int64_t v0, nv;
     int *adj, *deg;
+    unsigned long long *examined;
 };
 
 template <int G, int V, int U>
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(256) prune_kernel(PruneArgs a) {
     int *kept = reinterpret_cast<int *>(reinterpret_cast<uint64_t *>(smem) + (size_t)wpb * a.Wr) +
                 (size_t)warp * a.Wr;
     const int64_t stride = (int64_t)gridDim.x * wpb;
+    unsigned long long examined = 0;
     for (int64_t j = (int64_t)blockIdx.x * wpb + warp; j < a.nv; j += stride) {
         const int64_t v = a.v0 + j;
         const int *ci = a.cand_ids + j * a.C;
@@ -212,7 +214,8 @@ __global__ void __launch_bounds__(256) prune_kernel(PruneArgs a) {
             nk = 1;
         }
         __syncwarp();
-        for (int t = 1; t < cnt && nk < a.R; ++t) {
+        int t = 1;
+        for (; t < cnt && nk < a.R; ++t) {
             const int p = ci[t];
             const float dpv = cd[t];
             RowQuery<G, V> P;
@@ -226,10 +229,12 @@ __global__ void __launch_bounds__(256) prune_kernel(PruneArgs a) {
                 __syncwarp();
             }
         }
-        for (int t = lane; t < a.R; t += 32) a.adj[v * a.R + t] = t < nk ? kept[t] : -1;
+        examined += cnt > 0 ? t : 0;
+        for (int e = lane; e < a.R; e += 32) a.adj[v * a.R + e] = e < nk ? kept[e] : -1;
         if (lane == 0) a.deg[v] = nk;
         __syncwarp();
     }
+    if (a.examined != nullptr && lane == 0 && examined) atomicAdd(a.examined, examined);
 }
 
 cudaError_t launch_prune(const PruneLaunch &l, cudaStream_t st) {
@@ -247,6 +252,7 @@ cudaError_t launch_prune(const PruneLaunch &l, cudaStream_t st) {
     a.nv = l.nv;
     a.adj = l.adj;
     a.deg = l.deg;
+    a.examined = l.examined;
     const int wpb = 8;
     size_t smem = (size_t)wpb * a.Wr * 12;
     cudaError_t err = cudaSuccess;

@@ -38,6 +38,7 @@ struct nsg_index {
     double avg_degree = 0.0;
     int64_t n_fixup = 0;
     int64_t n_fixup_searches = 0;  // fix-ups whose speculative search was stale and ran again
+    int64_t prune_examined = 0;    // candidates the edge selection examined, all nodes
     float ms[6] = {0, 0, 0, 0, 0, 0};
 };
 
@@ -103,7 +104,7 @@ inline int default_steps(int L) { return 16 * L + 4096; }
 inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // Published SplitMix64 finaliser (Steele, Lea, Flood 2014): the random start
-// node of Alg. 2 line 2 is splitmix64(seed) mod n.
+// node of Alg. 2 is splitmix64(seed) mod n.
 inline uint64_t splitmix64(uint64_t x) {
     uint64_t z = x + 0x9e3779b97f4a7c15ULL;
     z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
@@ -212,7 +213,7 @@ nsg_status connect_run(const float *bp, int64_t n, int dp, int *adj, int *deg, i
 
 nsg_status collect_prune_all(const float *bp, int64_t n, int dp, const int *knn, int K, int nav, int L,
                              int R, int C, int *adj, int *deg, float *ms_collect, float *ms_prune,
-                             cudaStream_t st) {
+                             int64_t *examined, cudaStream_t st) {
     // candidate lists are materialised for a chunk of nodes at a time
     const size_t budget = size_t(2) << 30;
     int64_t chunk = (int64_t)(budget / ((size_t)C * 8 + 8));
@@ -220,9 +221,12 @@ nsg_status collect_prune_all(const float *bp, int64_t n, int dp, const int *knn,
     if (chunk < 1) chunk = 1;
     DevBuf<int> cid, ccnt;
     DevBuf<float> cd2;
+    DevBuf<unsigned long long> nexam;
     NSG_CK(cid.alloc((size_t)chunk * C));
     NSG_CK(cd2.alloc((size_t)chunk * C));
     NSG_CK(ccnt.alloc(chunk));
+    NSG_CK(nexam.alloc(1));
+    NSG_CK(cudaMemsetAsync(nexam.p, 0, sizeof(unsigned long long), st));
     cudaEvent_t ev[3];
     for (auto &e : ev) NSG_CK(cudaEventCreate(&e));
     float tc = 0, tp = 0;
@@ -263,6 +267,7 @@ nsg_status collect_prune_all(const float *bp, int64_t n, int dp, const int *knn,
         p.nv = nv;
         p.adj = adj;
         p.deg = deg;
+        p.examined = nexam.p;
         if (rc == NSG_OK) {
             e = nsg::launch_prune(p, st);
             if (e != cudaSuccess) rc = cuda_fail(e, "launch_prune");
@@ -279,6 +284,13 @@ nsg_status collect_prune_all(const float *bp, int64_t n, int dp, const int *knn,
     for (auto &e : ev) cudaEventDestroy(e);
     if (ms_collect) *ms_collect = tc;
     if (ms_prune) *ms_prune = tp;
+    if (examined && rc == NSG_OK) {
+        unsigned long long h = 0;
+        cudaError_t e = cudaMemcpyAsync(&h, nexam.p, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "prune counter");
+        *examined = (int64_t)h;
+    }
     return rc;
 }
 
@@ -592,7 +604,7 @@ nsg_status nsg_build(const float *base_dev, int64_t n, int32_t d, int32_t K, int
     // A5 + A6: search-collect-select per node
     if (!s)
         s = collect_prune_all(base.p, n, ix->dp, knn.p, K, ix->nav, L, R, C, adj.p, deg.p, &ix->ms[2],
-                              &ix->ms[3], st);
+                              &ix->ms[3], &ix->prune_examined, st);
     knn.alloc(0);  // release the kNN graph before the connectivity pass
     // A7: connectivity
     t0 = std::chrono::steady_clock::now();
@@ -1087,6 +1099,7 @@ nsg_status nsg_index_info(const nsg_index *idx, nsg_index_info_t *info) {
     info->has_u8 = idx->lowp[NSG_PREC_U8] ? (idx->lowp_exact[NSG_PREC_U8] ? 2 : 1) : 0;
     info->u8_lo = idx->lowp[NSG_PREC_U8] ? idx->lowp_lo[NSG_PREC_U8] : 0.0f;
     info->u8_scale = idx->lowp[NSG_PREC_U8] ? idx->lowp_scale[NSG_PREC_U8] : 0.0f;
+    info->prune_examined = idx->prune_examined;
     for (int p = 1; p <= 3; ++p)
         if (idx->lowp[p]) info->device_bytes += (int64_t)idx->n * idx->lowp_dpl[p] * (p == 1 ? 2 : 1);
     info->ms_knn = idx->ms[0];

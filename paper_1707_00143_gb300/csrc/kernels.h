@@ -106,6 +106,7 @@ struct PruneLaunch {
     int64_t v0, nv;
     int *adj;
     int *deg;
+    unsigned long long *examined = nullptr;  // nullable: += candidates examined over all nodes
 };
 cudaError_t launch_prune(const PruneLaunch &a, cudaStream_t st);
 

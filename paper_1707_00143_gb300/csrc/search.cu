@@ -1,5 +1,5 @@
 // search.cu -- Alg. 1 for a batch of queries (search on NSG, Section 3.5) and
-// the per-node search-and-collect of Alg. 2 (lines 5-8), one warp per unit.
+// the per-node search-and-collect of Alg. 2 (Section 3.4 iii), one warp per unit.
 #include <algorithm>
 #include <type_traits>
 
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(256) collect_kernel(CollectArgs a) {
         int csize = 0;
         SearchOut o = warp_alg1<true, false>(dist, GraphRef{a.knn, a.K}, a.nav, a.L, s, hmask, a.hshift,
                                              a.max_steps, v, a.C, csize);
-        // Alg. 2 line 7: v's nearest neighbours in G join the candidates
+        // Alg. 2: v's nearest neighbours in G join the candidates
         const int *row = a.knn + (int64_t)v * a.K;
         int m = 0;
         for (int b = 0; b < a.K; b += 32) {
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(256) collect_kernel(CollectArgs a) {
             dist(s.ids, m, s.keys);
             collect_merge(s, m, v, a.C, csize);
         }
-        // Alg. 2 line 8: sorted candidates, cut to C
+        // Alg. 2: sorted candidates, cut to C
         for (int t = lane; t < a.C; t += 32) {
             uint64_t e = t < csize ? s.clist[t] : KEY_INF;
             a.cand_ids[j * a.C + t] = t < csize ? kid(e) : -1;

@@ -11,10 +11,10 @@
 //
 // The same routine serves
 //   * search on the NSG from the navigating node (Section 3.5),
-//   * search-and-collect on the kNN graph (Alg. 2 lines 5-6): every computed
+//   * search-and-collect on the kNN graph (Alg. 2, Section 3.4 iii): every computed
 //     key except the node itself is also merged into a collect list of the C
 //     smallest keys,
-//   * the connectivity pass (Alg. 2 line 26): speculative searches that also
+//   * the connectivity pass (Alg. 2, Section 3.4 iv): speculative searches that also
 //     log the ids they expand, and re-searches on a graph the same kernel is
 //     editing (plain coherent loads instead of the read-only path).
 #pragma once

@@ -121,6 +121,20 @@ def test_build_bit_exact(nsg, tiny):
     assert info["max_degree"] <= R
 
 
+def test_build_prune_examined_count(nsg, tiny):
+    # the edge selection examines a node's candidates in key order until R are
+    # kept (then up to the R-th kept one) or the list ends; the oracle's
+    # candidate lists and rows give that count per node
+    base, ref = tiny["base"], tiny["ref"]
+    want = 0
+    for v in range(len(base)):
+        cid, cd, cnt, _, _ = oracle.collect(ref["knn"], base, ref["nav"], v, LB, CAP)
+        row, deg = oracle.prune(base, cid[:cnt], cd[:cnt], R)
+        want += int(np.nonzero(cid[:cnt] == row[R - 1])[0][0]) + 1 if deg == R else cnt
+    info = nsg.nsg_build(T(base), K, LB, R, CAP, seed=0).info()
+    assert info["prune_examined"] == want
+
+
 @pytest.mark.parametrize("k,L", [(10, 50), (1, 10), (16, 16), (100, 137), (10, 400), (10, 1024)])
 def test_search_bit_exact(nsg, tiny, k, L):
     base, q, ref = tiny["base"], tiny["q"], tiny["ref"]

@@ -41,9 +41,9 @@ def test_collect_contains_knn_row_and_excludes_v():
         got = ids[:cnt]
         assert v not in got.tolist()
         assert len(set(got.tolist())) == cnt  # unique
-        assert set(knn[v].tolist()) <= set(got.tolist())  # Alg. 2 line 7
+        assert set(knn[v].tolist()) <= set(got.tolist())  # Alg. 2: v's kNN neighbours join the candidates
         keys = list(zip(dist[:cnt].tolist(), got.tolist()))
-        assert keys == sorted(keys)  # Alg. 2 line 8
+        assert keys == sorted(keys)  # Alg. 2: candidates sorted by key
         # every distance is the exact squared distance to x_v (integer data)
         exact = ((base[got].astype(np.float64) - base[v]) ** 2).sum(1)
         assert np.array_equal(dist[:cnt].astype(np.float64), exact)
