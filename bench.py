@@ -163,11 +163,15 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sm)}
 
 
-def kernel_source_hash():
-    """Hash of the search kernel's code with comments and blank lines removed,
-    so that the hash changes with the code and not with its documentation."""
+SEARCH_SOURCES = ("common.cuh", "search_core.cuh", "lowp.cuh", "search.cu")
+PRUNE_SOURCES = ("common.cuh", "search_core.cuh", "build.cu")
+
+
+def kernel_source_hash(files=SEARCH_SOURCES):
+    """Hash of a kernel's code with comments and blank lines removed, so that
+    the hash changes with the code and not with its documentation."""
     h = hashlib.sha256()
-    for f in ("common.cuh", "search_core.cuh", "lowp.cuh", "search.cu"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1707_00143_gb300", "csrc", f)) as fh:
             src = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
         lines = (re.sub(r"//.*", "", ln).rstrip() for ln in src.splitlines())
@@ -181,6 +185,11 @@ def kernel_source_hash():
 # the hash, and `traffic` is null until re-measured.
 NCU_TRAFFIC = {
     ("ae7f3d5fded47695", "sift", "u8", 150): (1_668_171_264 + 10_440_960) / 10_000,
+}
+# the same for the MRNG edge selection of the build, per node, keyed by
+# (source hash, workload): profiles/prune_kernel_sift1m.md
+PRUNE_TRAFFIC = {
+    ("7c97dbc98864b866", "sift"): (18_417_009_408 + 135_907_328 + 15_953_364_992 + 113_341_440) / 1_000_000,
 }
 
 
@@ -477,7 +486,9 @@ def main():
     prune_roofline = {"bound": "hbm", "achieved": prune_bytes / (info["ms_prune"] / 1e3) / 1e9 if info["ms_prune"] else None,
                       "peak": peak, "unit": "GB/s", "peak_kind": peak_kind, "kernel": "prune_kernel",
                       "algorithmic_bytes": prune_bytes, "examined_per_node": info["prune_examined"] / n,
-                      "ms": info["ms_prune"]}
+                      "ms": info["ms_prune"], "kernel_src": kernel_source_hash(PRUNE_SOURCES)}
+    ptr = PRUNE_TRAFFIC.get((prune_roofline["kernel_src"], args.workload))
+    prune_roofline["traffic"] = ptr * n if ptr else None
     if prune_roofline["achieved"] is not None:
         prune_roofline["frac"] = prune_roofline["achieved"] / peak
 

@@ -189,7 +189,8 @@ nsg_status nsg_collect(const float *base_dev, int64_t n, int32_t d, const int32_
  * A6. MRNG edge selection (Alg. 2; Def. MRNG and Section 3.3) for
  *   nodes v0 .. v0+nv-1 over their sorted candidates: the first candidate is
  *   kept; a later candidate p is dropped when some kept r has
- *   d2(p, r) < d2(p, v); stop at R kept.  Inputs as written by nsg_collect.
+ *   d2(p, r) < d2(p, v); stop at R kept.  Inputs as written by nsg_collect
+ *   (a node's list ends at its count or at its first negative id).
  *   adj_dev [n][R] i32 and deg_dev [n] i32: rows v0.. are written (-1 padded).
  * ------------------------------------------------------------------------- */
 nsg_status nsg_prune(const float *base_dev, int64_t n, int32_t d, const int32_t *cand_ids_dev,

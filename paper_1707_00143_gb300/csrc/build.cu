@@ -179,7 +179,15 @@ cudaError_t launch_navigate(const float *base, int64_t n, int d, const int *knn,
 // MRNG edge selection (Alg. 2; Section 3.3), one warp per node.  Candidates are
 // already sorted by key; the first is kept; a later candidate p is occluded
 // when d2(p, r) < d2(p, v) for a kept r (r in the open lune of vp); stop at R.
-// The warp holds p's row; G-lane groups compute d2(p, r) for the kept rows.
+//
+// The warp takes the candidates in batches of NB = (32 / G) * B: each G-lane
+// group holds B candidate rows in registers (batch position b * (32/G) + grp).
+// The kept rows are read once per batch, U at a time, and every group measures
+// them against its B candidates; the pass ends early once every candidate of
+// the batch is occluded.  The survivors are then taken in candidate order:
+// the first is kept, and the later survivors are measured against it (the
+// kept set a sequential scan would have at their turn), and so on.  Results,
+// and the count of candidates examined, equal the one-at-a-time scan.
 // ---------------------------------------------------------------------------
 struct PruneArgs {
     const float4 *base4;
@@ -193,49 +201,149 @@ struct PruneArgs {
     unsigned long long *examined;
 };
 
-template <int G, int V, int U>
+// Batch positions (b * P + g) whose flag is set in group g's lane 0, as a mask.
+template <int G, int B>
+__device__ __forceinline__ unsigned batch_mask(const bool (&f)[B]) {
+    constexpr int P = 32 / G;
+    const bool lead = lane_id() % G == 0;
+    unsigned m = 0;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const unsigned bal = __ballot_sync(NSG_FULL, lead && f[b]);
+#pragma unroll
+        for (int g = 0; g < P; ++g) m |= ((bal >> (g * G)) & 1u) << (b * P + g);
+    }
+    return m;
+}
+
+template <int G, int V, int U, int B>
 __global__ void __launch_bounds__(256) prune_kernel(PruneArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int P = 32 / G, NB = P * B;
+    static_assert(NB <= 32, "batch mask holds 32 positions");
     const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    const unsigned lane = lane_id();
-    uint64_t *keys = reinterpret_cast<uint64_t *>(smem) + (size_t)warp * a.Wr;
-    int *kept = reinterpret_cast<int *>(reinterpret_cast<uint64_t *>(smem) + (size_t)wpb * a.Wr) +
-                (size_t)warp * a.Wr;
+    const int lane = (int)lane_id(), grp = lane / G, sub = lane % G;
+    int *kept = reinterpret_cast<int *>(smem) + (size_t)warp * a.Wr;
     const int64_t stride = (int64_t)gridDim.x * wpb;
     unsigned long long examined = 0;
     for (int64_t j = (int64_t)blockIdx.x * wpb + warp; j < a.nv; j += stride) {
         const int64_t v = a.v0 + j;
         const int *ci = a.cand_ids + j * a.C;
         const float *cd = a.cand_d2 + j * a.C;
-        const int cnt = a.cand_count != nullptr ? min(max(a.cand_count[j], 0), a.C) : a.C;
-        int nk = 0;
+        int cnt = a.cand_count != nullptr ? min(max(a.cand_count[j], 0), a.C) : a.C;
+        if (cnt > 0 && ci[0] < 0) cnt = 0;  // a negative id ends the list
+        int nk = 0, t = 0;                  // kept; candidates examined
         if (cnt > 0) {
             if (lane == 0) kept[0] = ci[0];
             nk = 1;
+            t = 1;
         }
         __syncwarp();
-        int t = 1;
-        for (; t < cnt && nk < a.R; ++t) {
-            const int p = ci[t];
-            const float dpv = cd[t];
-            RowQuery<G, V> P;
-            P.load_row(a.base4 + (int64_t)p * a.dp4, a.dp4);
-            rows_dist<G, V, U>(P, a.base4, a.dp4, kept, nk, keys);
-            bool occ = false;
-            for (int b = lane; b < nk; b += 32) occ |= kd2(keys[b]) < dpv;
-            if (!__any_sync(NSG_FULL, occ)) {
-                if (lane == 0) kept[nk] = p;
-                ++nk;
-                __syncwarp();
+        while (t < cnt && nk < a.R) {
+            float4 q[B][V];
+            float pdv[B];
+            bool occ[B];
+            int id[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int c = t + b * P + grp;
+                id[b] = c < cnt ? ci[c] : 0;
+                occ[b] = id[b] < 0;
             }
+            const unsigned neg = batch_mask<G, B>(occ);
+            if (neg) cnt = t + __ffs(neg) - 1;  // a negative id ends the list
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int c = t + b * P + grp;
+                const bool valid = c < cnt;
+                pdv[b] = valid ? cd[c] : 0.0f;
+                occ[b] = !valid;
+                const float4 *row = a.base4 + (int64_t)(valid ? id[b] : 0) * a.dp4;
+#pragma unroll
+                for (int u = 0; u < V; ++u) {
+                    const int k = u * G + sub;
+                    q[b][u] = (valid && k < a.dp4) ? __ldg(row + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            // against the kept set as it was before the batch
+            for (int i0 = 0; i0 < nk; i0 += U) {
+                bool all = true;
+#pragma unroll
+                for (int b = 0; b < B; ++b) all &= occ[b];
+                if (__all_sync(NSG_FULL, all)) break;
+                float4 x[U][V];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u;
+                    const float4 *row = a.base4 + (int64_t)(i < nk ? kept[i] : 0) * a.dp4;
+#pragma unroll
+                    for (int w = 0; w < V; ++w) {
+                        const int k = w * G + sub;
+                        x[u][w] = (i < nk && k < a.dp4) ? __ldg(row + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int b = 0; b < B; ++b) {
+                        float s = 0.0f;
+#pragma unroll
+                        for (int w = 0; w < V; ++w) s += sq4(x[u][w], q[b][w]);
+                        s = group_sum<G>(s);
+                        if (i0 + u < nk && s < pdv[b]) occ[b] = true;
+                    }
+            }
+            // survivors in candidate order, each measured against the ones kept before it
+            bool live_f[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) live_f[b] = !occ[b];
+            unsigned live = batch_mask<G, B>(live_f);
+            int stop = -1;
+            while (live) {
+                const int pos = __ffs(live) - 1;
+                live &= live - 1u;
+                const int pj = ci[t + pos];
+                if (lane == 0) kept[nk] = pj;
+                ++nk;
+                if (nk == a.R) {
+                    stop = pos;
+                    break;
+                }
+                if (!live) break;
+                const float4 *row = a.base4 + (int64_t)pj * a.dp4;
+                float4 x[V];
+#pragma unroll
+                for (int w = 0; w < V; ++w) {
+                    const int k = w * G + sub;
+                    x[w] = k < a.dp4 ? __ldg(row + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                bool hit[B];
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                    float s = 0.0f;
+#pragma unroll
+                    for (int w = 0; w < V; ++w) s += sq4(x[w], q[b][w]);
+                    s = group_sum<G>(s);
+                    hit[b] = s < pdv[b];
+                }
+                live &= ~batch_mask<G, B>(hit);
+            }
+            __syncwarp();
+            t = stop >= 0 ? t + stop + 1 : min(t + NB, cnt);
         }
-        examined += cnt > 0 ? t : 0;
+        examined += (unsigned long long)t;
         for (int e = lane; e < a.R; e += 32) a.adj[v * a.R + e] = e < nk ? kept[e] : -1;
         if (lane == 0) a.deg[v] = nk;
         __syncwarp();
     }
     if (a.examined != nullptr && lane == 0 && examined) atomicAdd(a.examined, examined);
 }
+
+// Candidate rows held per lane group: two while they fit in 32 float4s.
+template <int V>
+struct PruneBatch {
+    static constexpr int value = V <= 8 ? 2 : 1;
+};
 
 cudaError_t launch_prune(const PruneLaunch &l, cudaStream_t st) {
     if (l.nv <= 0) return cudaSuccess;
@@ -254,10 +362,10 @@ cudaError_t launch_prune(const PruneLaunch &l, cudaStream_t st) {
     a.deg = l.deg;
     a.examined = l.examined;
     const int wpb = 8;
-    size_t smem = (size_t)wpb * a.Wr * 12;
+    size_t smem = (size_t)wpb * a.Wr * 4;
     cudaError_t err = cudaSuccess;
     NSG_DISPATCH_DP4(a.dp4, {
-        auto kern = prune_kernel<G_, V_, U_>;
+        auto kern = prune_kernel<G_, V_, U_, PruneBatch<V_>::value>;
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err == cudaSuccess) {
             int per_sm = 0;

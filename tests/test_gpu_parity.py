@@ -88,6 +88,16 @@ def test_collect_then_prune_all_nodes_bit_exact(nsg, tiny):
     assert np.array_equal(H(adj), tiny["adj0"])
 
 
+def test_prune_list_ends_at_negative_id(nsg, tiny):
+    # counts of C with -1 padding after each list: the padding ends the list
+    base, ref = tiny["base"], tiny["ref"]
+    ids, d2, cnt, _ = nsg.nsg_collect(T(base), T(ref["knn"]), ref["nav"], LB, CAP)
+    full = torch.full_like(cnt, CAP)
+    adj, deg = nsg.nsg_prune(T(base), ids, d2, full, R)
+    assert np.array_equal(H(deg), tiny["deg0"])
+    assert np.array_equal(H(adj), tiny["adj0"])
+
+
 def test_prune_chunked_offsets(nsg, tiny):
     # rows v0..v0+nv-1 only; other rows untouched
     base, ref = tiny["base"], tiny["ref"]
