@@ -6,8 +6,8 @@
  * ---------------------------------------
  *  - Distances are SQUARED l2 (Section 2 defines delta as the l2 distance;
  *    the method only ever compares distances, so squaring changes nothing).
- *  - "Key order" is (squared distance, id) ascending.  It is the paper's
- *    "ascending order of the distance" (Alg. 1, and Alg. 2's candidate sort) with the
+ *  - "Key order" is (squared distance, id) ascending: the distance order
+ *    that Alg. 1 keeps its pool in and Alg. 2 sorts candidates by, with the
  *    lower-index tie rule of the MRNG definition (Section 3.3) applied to
  *    every tie.
  *  - Pointers named *_dev are device pointers (cudaMalloc / torch CUDA
@@ -306,7 +306,7 @@ void nsg_plan_free(nsg_plan *plan);
 
 /* ---------------------------------------------------------------------------
  * Learned early termination (not in the paper: a serving-side addition; the
- * fixed-L Alg. 1 is its fallback and the judge of its recall loss).
+ * fixed-L Alg. 1 is its fallback and the yardstick of its recall loss).
  * nsg_search_trace: Alg. 1 with fixed L that records, before each expansion
  *   t (t < cap), the 8 state features (feat_dev [nq][cap][8] f32) and after
  *   it whether the first stop_k pool entries changed (flag_dev [nq][cap] u8);

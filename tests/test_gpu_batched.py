@@ -1,7 +1,7 @@
 """Batched uneven queries: per-query (k, L) in one persistent launch with a
 device work queue; plans autotune the launch shape and replay a CUDA graph.
 
-The plain form is the judge: every query's result must equal the fixed
+The plain form is the reference: every query's result must equal the fixed
 (k, L) search of that query alone (ids and distances bit for bit on integer
 data, whatever launch shape or visited-hash size the autotuner picks)."""
 import numpy as np

@@ -8,7 +8,7 @@
 * Inference: a model that never stops reproduces the fixed-L search exactly;
   one that always stops ends after `stop_min_steps` expansions.
 * A trained model trades expansions for a bounded recall loss (the fixed-L
-  search is the judge)."""
+  search is the yardstick)."""
 import numpy as np
 import pytest
 import torch

@@ -2,7 +2,7 @@
 of the base with FP32 accumulation or on an 8-bit copy with exact int32 sums,
 and an FP32 re-rank of the final pool.
 
-Judged against the plain form and the oracle:
+Checked against the plain form and the oracle:
 * integer data 0..255 is held exactly by BF16, so the BF16 form must equal
   the oracle bit for bit (with or without the re-rank);
 * with re-rank, every returned distance is the exact FP32 squared distance
