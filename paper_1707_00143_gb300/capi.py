@@ -79,6 +79,7 @@ SIGNATURES = [
     ("nsg_index_from_graph", [P, i64, i32, P, P, i32, i32, P, P], i32),
     ("nsg_search", [P, P, i64, i32, i32, P, P, P], i32),
     ("nsg_search_ex", [P, P, i64, i32, i32, P, P, P, P, P, P, P], i32),
+    ("nsg_search_host", [P, P, i64, i32, i32, P, P, P, P], i32),
     ("nsg_recall", [P, i32, P, i32, i64, i32, P, P], i32),
     ("nsg_search_trace", [P, P, i64, i32, i32, P, P, P, P, P, i32, P], i32),
     ("nsg_search_batched", [P, P, i64, P, P, i32, i32, P, P, P, P, P], i32),
@@ -127,6 +128,12 @@ def _stream():
 def _dev(t, dtype):
     if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
         raise ValueError(f"expected a contiguous CUDA {dtype} tensor")
+    return t
+
+
+def _host(t, dtype):
+    if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous host {dtype} tensor")
     return t
 
 
@@ -284,6 +291,21 @@ class Index:
                                    _ptr(out.get("d2")), _ptr(out.get("n_expand")), _ptr(out.get("n_dist")),
                                    _ptr(out.get("status")), _stream()), "nsg_search_ex")
         return out
+
+    def search_host(self, queries, k, L, params=None, ids=None, d2=None):
+        """nsg_search_ex on host tensors (page-locked for copy/compute
+        overlap): queries [nq][d] float32 in; ids [nq][k] int32 and d2
+        (optional) out.  Returns when the results are in host memory."""
+        queries = _host(queries, torch.float32)
+        nq = queries.shape[0]
+        pin = queries.is_pinned()
+        ids = torch.empty((nq, k), dtype=torch.int32, pin_memory=pin) if ids is None else _host(ids, torch.int32)
+        if d2 is not None:
+            d2 = _host(d2, torch.float32)
+        p = params if params is not None else SearchParams(0, 0, PREC_F32, 0)
+        _check(lib().nsg_search_host(self.h, _ptr(queries), nq, k, L, C.byref(p), _ptr(ids), _ptr(d2),
+                                     _stream()), "nsg_search_host")
+        return dict(ids=ids, d2=d2)
 
     def search_trace(self, queries, k, L, cap, params=None):
         """Fixed-L search recording per-step stop features and change flags."""

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "kernels.h"
@@ -40,6 +41,17 @@ struct nsg_index {
     int64_t n_fixup_searches = 0;  // fix-ups whose speculative search was stale and ran again
     int64_t prune_examined = 0;    // candidates the edge selection examined, all nodes
     float ms[6] = {0, 0, 0, 0, 0, 0};
+    // nsg_search_host: device staging for `host_cap` queries, two streams,
+    // a step-cap flag; one call at a time
+    mutable std::mutex host_mu;
+    mutable int64_t host_cap = 0;
+    mutable int host_k = 0;
+    mutable float *host_q = nullptr;
+    mutable int *host_ids = nullptr;
+    mutable float *host_d2 = nullptr;
+    mutable int *host_flag = nullptr;
+    mutable cudaStream_t host_st[2] = {nullptr, nullptr};
+    mutable cudaEvent_t host_ev = nullptr;
 };
 
 namespace {
@@ -320,6 +332,13 @@ void destroy(nsg_index *ix) {
     if (ix->work) cudaFree(ix->work);
     for (void *p : ix->lowp)
         if (p) cudaFree(p);
+    if (ix->host_q) cudaFree(ix->host_q);
+    if (ix->host_ids) cudaFree(ix->host_ids);
+    if (ix->host_d2) cudaFree(ix->host_d2);
+    if (ix->host_flag) cudaFree(ix->host_flag);
+    for (cudaStream_t h : ix->host_st)
+        if (h) cudaStreamDestroy(h);
+    if (ix->host_ev) cudaEventDestroy(ix->host_ev);
     delete ix;
 }
 
@@ -779,6 +798,81 @@ nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t
                                status_dev, l);
     if (s || nq == 0) return s;
     return launch_dynamic(idx, l, S(stream));
+}
+
+nsg_status nsg_search_host(const nsg_index *idx, const float *queries_host, int64_t nq, int32_t k, int32_t L,
+                           const nsg_search_params *params, int32_t *ids_host, float *d2_host, void *stream) {
+    if (!idx || (nq > 0 && (!queries_host || !ids_host))) return NSG_EINVAL;
+    // validate with placeholder device pointers (nothing is launched here)
+    nsg::SearchLaunch l;
+    const float *qph = reinterpret_cast<const float *>(16);
+    int *iph = reinterpret_cast<int *>(16);
+    nsg_status s = make_search(idx, qph, nq, k, L, params, iph, nullptr, nullptr, nullptr, nullptr, l);
+    if (s || nq == 0) return s;
+    std::lock_guard<std::mutex> lock(idx->host_mu);
+    const int d = idx->d;
+    if (nq > idx->host_cap || k > idx->host_k) {
+        const int64_t cap = nq > idx->host_cap ? nq : idx->host_cap;
+        const int kc = k > idx->host_k ? k : idx->host_k;
+        cudaFree(idx->host_q);
+        cudaFree(idx->host_ids);
+        cudaFree(idx->host_d2);
+        idx->host_q = nullptr;
+        idx->host_ids = nullptr;
+        idx->host_d2 = nullptr;
+        idx->host_cap = 0;
+        idx->host_k = 0;
+        NSG_CK(cudaMalloc(&idx->host_q, sizeof(float) * cap * d));
+        NSG_CK(cudaMalloc(&idx->host_ids, sizeof(int) * cap * kc));
+        NSG_CK(cudaMalloc(&idx->host_d2, sizeof(float) * cap * kc));
+        idx->host_cap = cap;
+        idx->host_k = kc;
+    }
+    if (!idx->host_flag) NSG_CK(cudaMalloc(&idx->host_flag, sizeof(int)));
+    for (cudaStream_t &h : idx->host_st)
+        if (!h) NSG_CK(cudaStreamCreateWithFlags(&h, cudaStreamNonBlocking));
+    if (!idx->host_ev) NSG_CK(cudaEventCreateWithFlags(&idx->host_ev, cudaEventDisableTiming));
+    // earlier work on the caller's stream first
+    NSG_CK(cudaMemsetAsync(idx->host_flag, 0, sizeof(int), S(stream)));
+    NSG_CK(cudaEventRecord(idx->host_ev, S(stream)));
+    for (cudaStream_t h : idx->host_st) NSG_CK(cudaStreamWaitEvent(h, idx->host_ev, 0));
+    const int chunks = nq >= 8192 ? 4 : (nq >= 2048 ? 2 : 1);
+    const int64_t per = (nq + chunks - 1) / chunks;
+    // on any error the streams are still drained before returning, so no copy
+    // touches the caller's host buffers after the call
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < chunks && e == cudaSuccess && s == NSG_OK; ++c) {
+        const int64_t q0 = c * per, m = nq - q0 < per ? nq - q0 : per;
+        if (m <= 0) break;
+        cudaStream_t h = idx->host_st[c & 1];
+        float *qd = idx->host_q + q0 * d;
+        int *id = idx->host_ids + q0 * k;
+        float *dd = idx->host_d2 + q0 * k;
+        e = cudaMemcpyAsync(qd, queries_host + q0 * d, sizeof(float) * m * d, cudaMemcpyHostToDevice, h);
+        if (e != cudaSuccess) break;
+        nsg::SearchLaunch lc = l;
+        lc.queries = qd;
+        lc.nq = m;
+        lc.ids = id;
+        lc.d2 = d2_host ? dd : nullptr;
+        lc.status = nullptr;
+        lc.any_capped = idx->host_flag;
+        s = launch_dynamic(idx, lc, h);
+        if (s) break;
+        e = cudaMemcpyAsync(ids_host + q0 * k, id, sizeof(int) * m * k, cudaMemcpyDeviceToHost, h);
+        if (e == cudaSuccess && d2_host)
+            e = cudaMemcpyAsync(d2_host + q0 * k, dd, sizeof(float) * m * k, cudaMemcpyDeviceToHost, h);
+    }
+    for (cudaStream_t h : idx->host_st) {
+        const cudaError_t se = cudaStreamSynchronize(h);
+        if (e == cudaSuccess) e = se;
+    }
+    if (s) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "nsg_search_host");
+    int capped = 0;
+    NSG_CK(cudaMemcpyAsync(&capped, idx->host_flag, sizeof(int), cudaMemcpyDeviceToHost, idx->host_st[0]));
+    NSG_CK(cudaStreamSynchronize(idx->host_st[0]));
+    return capped ? NSG_ESTEPCAP : NSG_OK;
 }
 
 }  // extern "C"

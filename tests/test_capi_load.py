@@ -62,6 +62,7 @@ def test_validation_rejects_before_any_launch(libnsg):
     assert libnsg.nsg_build(fake, 100, 8, 4, 10, 4, 8, 0, None, None) == EINVAL
     assert libnsg.nsg_knn_init(fake, 1, 8, 1, fake, None, None) == EINVAL  # n < 2
     assert libnsg.nsg_search(None, fake, 10, 5, 10, fake, None, None) == EINVAL
+    assert libnsg.nsg_search_host(None, fake, 10, 5, 10, None, fake, None, None) == EINVAL
     assert libnsg.nsg_collect(fake, 100, 6, fake, 4, 0, 10, 8, 0, 10, fake, fake, fake, None, None) == EINVAL
     assert libnsg.nsg_recall(fake, 5, fake, 5, 3, 10, fake, None) == EINVAL  # k > ld
     info = capi.IndexInfo()
