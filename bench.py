@@ -4,8 +4,11 @@
 Workload: the SIFT-shaped synthetic set (1,000,000 x 128 integer values 0..255
 from a 100-component Gaussian mixture, 10,000 queries), index built with the
 paper's Alg. 2 at K=100, L=40, R=50, C=500.  The pool size L is swept over
-100, 125, ..., 400 (k=100); the reported point is the highest-QPS L whose
-mean recall@10 (Eq. 1, against the exact ground truth) is >= 0.95.
+100, 125, ..., 400 and 500..1000 (k=100), and between the last grid point
+below a recall target and the first one above it the smallest integer L
+reaching the target is found by bisection; the reported point is the
+highest-QPS L whose mean recall@10 (Eq. 1, against the exact ground truth)
+is >= 0.95.
 
 Forms: plain (FP32 traversal, exactly Alg. 1), the precision forms (BF16 or
 FP8-e4m3 traversal distances with FP32 accumulation, or an 8-bit copy with
@@ -20,7 +23,7 @@ A step = one nsg_search_ex launch over the whole 10,000-query batch, inputs
 resident in HBM.  The base (512 MB) is larger than L2 (129 MB).
 `e2e` repeats the step through the C ABI's host-buffer call (nsg_search_host)
 on page-locked host memory: host->device copy of the queries, search,
-device->host copy of the ids, chunked over two streams inside the call.
+device->host copy of the ids, all inside the call.
 
 Multi-GPU: queries are independent, so each rank searches its own batch on
 its own replica of the index (weak scaling, no collective on the data path).
@@ -330,7 +333,29 @@ def main():
     def recall10(o):
         return capi.nsg_recall(o["ids"][:, :10].contiguous(), gt, 10).sum().item() / (10.0 * nq)
 
-    # sweep L per form: recall@10 and a quick timing per point
+    def refine(pts, prm, t):
+        """Smallest integer L between the last grid point below recall t and
+        the first one at or above it that still reaches t (bisection, recall
+        growing with L); the grid point itself when no smaller L does."""
+        pts = sorted(pts, key=lambda p: p["L"])
+        above = [i for i, p in enumerate(pts) if p["recall10"] >= t]
+        if not above or above[0] == 0:
+            return None
+        lo, hi, hi_rec = pts[above[0] - 1]["L"], pts[above[0]]["L"], pts[above[0]]["recall10"]
+        grid_hi = hi
+        while hi - lo > 1:
+            mid = (lo + hi) // 2
+            r = recall10(run(mid, prm))
+            if r >= t:
+                hi, hi_rec = mid, r
+            else:
+                lo = mid
+        if hi == grid_hi:
+            return None
+        return {"L": hi, "recall10": hi_rec, "qps": nq / (timed(prm, hi, 2) / 1e3), "refined": True}
+
+    # sweep L per form: recall@10 and a quick timing per point, then the
+    # smallest L reaching each recall target between two grid points
     sweeps, best = {}, {}
     for name, prm in forms.items():
         pts = []
@@ -338,6 +363,11 @@ def main():
             rec = recall10(run(L, prm))
             ms = timed(prm, L, 2)
             pts.append({"L": L, "recall10": rec, "qps": nq / (ms / 1e3)})
+        for t in RECALL_TARGETS:
+            p = refine(pts, prm, t)
+            if p is not None and all(q["L"] != p["L"] for q in pts):
+                pts.append(p)
+        pts.sort(key=lambda p: p["L"])
         sweeps[name] = pts
         ok = [p for p in pts if p["recall10"] >= TARGET]
         best[name] = max(ok, key=lambda p: p["qps"]) if ok else None

@@ -269,16 +269,14 @@ nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t
 /* ---------------------------------------------------------------------------
  * nsg_search_host: nsg_search_ex on HOST buffers (not in the paper: the
  *   serving-side call).  queries_host [nq][d] f32 in, ids_host [nq][k] i32
- *   out, d2_host [nq][k] f32 out (nullable); page-locked host memory gives
- *   full copy/compute overlap, pageable memory works but serialises its
- *   copies.  The batch is cut into up to 4 chunks (one when nq < 2048) that
- *   alternate over two streams owned by the index: a chunk's host->device
- *   copy, search and device->host copy are ordered on its stream, so one
- *   chunk's copies overlap another's search.  Device staging buffers belong
- *   to the index (grown on demand, kept until nsg_free); calls on one index
- *   are serialised.  Work queued on `stream` before the call completes first.
- *   Synchronous: returns once the results are in host memory, with
- *   NSG_ESTEPCAP if any query hit its step cap (its partial result is kept).
+ *   out, d2_host [nq][k] f32 out (nullable); page-locked host memory copies
+ *   fastest, pageable memory works.  On `stream`: one host->device copy of
+ *   the queries into device staging owned by the index (grown on demand,
+ *   kept until nsg_free), one search launch over the whole batch, the
+ *   device->host copies of the results.  Calls on one index are serialised.
+ *   Synchronous: returns once the results are in host memory (on an error,
+ *   after the stream has drained), with NSG_ESTEPCAP if any query hit its
+ *   step cap (its partial result is kept).
  * ------------------------------------------------------------------------- */
 nsg_status nsg_search_host(const nsg_index *idx, const float *queries_host, int64_t nq, int32_t k,
                            int32_t L, const nsg_search_params *params, int32_t *ids_host,

@@ -41,8 +41,8 @@ struct nsg_index {
     int64_t n_fixup_searches = 0;  // fix-ups whose speculative search was stale and ran again
     int64_t prune_examined = 0;    // candidates the edge selection examined, all nodes
     float ms[6] = {0, 0, 0, 0, 0, 0};
-    // nsg_search_host: device staging for `host_cap` queries, two streams,
-    // a step-cap flag; one call at a time
+    // nsg_search_host: device staging for `host_cap` queries of up to
+    // `host_k` results and a step-cap flag; one call at a time
     mutable std::mutex host_mu;
     mutable int64_t host_cap = 0;
     mutable int host_k = 0;
@@ -50,8 +50,6 @@ struct nsg_index {
     mutable int *host_ids = nullptr;
     mutable float *host_d2 = nullptr;
     mutable int *host_flag = nullptr;
-    mutable cudaStream_t host_st[2] = {nullptr, nullptr};
-    mutable cudaEvent_t host_ev = nullptr;
 };
 
 namespace {
@@ -336,9 +334,6 @@ void destroy(nsg_index *ix) {
     if (ix->host_ids) cudaFree(ix->host_ids);
     if (ix->host_d2) cudaFree(ix->host_d2);
     if (ix->host_flag) cudaFree(ix->host_flag);
-    for (cudaStream_t h : ix->host_st)
-        if (h) cudaStreamDestroy(h);
-    if (ix->host_ev) cudaEventDestroy(ix->host_ev);
     delete ix;
 }
 
@@ -829,49 +824,34 @@ nsg_status nsg_search_host(const nsg_index *idx, const float *queries_host, int6
         idx->host_k = kc;
     }
     if (!idx->host_flag) NSG_CK(cudaMalloc(&idx->host_flag, sizeof(int)));
-    for (cudaStream_t &h : idx->host_st)
-        if (!h) NSG_CK(cudaStreamCreateWithFlags(&h, cudaStreamNonBlocking));
-    if (!idx->host_ev) NSG_CK(cudaEventCreateWithFlags(&idx->host_ev, cudaEventDisableTiming));
-    // earlier work on the caller's stream first
-    NSG_CK(cudaMemsetAsync(idx->host_flag, 0, sizeof(int), S(stream)));
-    NSG_CK(cudaEventRecord(idx->host_ev, S(stream)));
-    for (cudaStream_t h : idx->host_st) NSG_CK(cudaStreamWaitEvent(h, idx->host_ev, 0));
-    const int chunks = nq >= 8192 ? 4 : (nq >= 2048 ? 2 : 1);
-    const int64_t per = (nq + chunks - 1) / chunks;
-    // on any error the streams are still drained before returning, so no copy
-    // touches the caller's host buffers after the call
-    cudaError_t e = cudaSuccess;
-    for (int c = 0; c < chunks && e == cudaSuccess && s == NSG_OK; ++c) {
-        const int64_t q0 = c * per, m = nq - q0 < per ? nq - q0 : per;
-        if (m <= 0) break;
-        cudaStream_t h = idx->host_st[c & 1];
-        float *qd = idx->host_q + q0 * d;
-        int *id = idx->host_ids + q0 * k;
-        float *dd = idx->host_d2 + q0 * k;
-        e = cudaMemcpyAsync(qd, queries_host + q0 * d, sizeof(float) * m * d, cudaMemcpyHostToDevice, h);
-        if (e != cudaSuccess) break;
-        nsg::SearchLaunch lc = l;
-        lc.queries = qd;
-        lc.nq = m;
-        lc.ids = id;
-        lc.d2 = d2_host ? dd : nullptr;
-        lc.status = nullptr;
-        lc.any_capped = idx->host_flag;
-        s = launch_dynamic(idx, lc, h);
-        if (s) break;
-        e = cudaMemcpyAsync(ids_host + q0 * k, id, sizeof(int) * m * k, cudaMemcpyDeviceToHost, h);
-        if (e == cudaSuccess && d2_host)
-            e = cudaMemcpyAsync(d2_host + q0 * k, dd, sizeof(float) * m * k, cudaMemcpyDeviceToHost, h);
+    // one copy in, one search over the whole batch, one copy out, on the
+    // caller's stream.  Splitting the batch over two streams to overlap the
+    // copies was measured slower (each smaller launch ends in its own tail of
+    // long queries, while the copies are ~1 % of the step on this host link).
+    // On any error the stream is still drained before returning, so no copy
+    // touches the caller's host buffers after the call.
+    cudaStream_t st = S(stream);
+    cudaError_t e = cudaMemsetAsync(idx->host_flag, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(idx->host_q, queries_host, sizeof(float) * nq * d, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        l.queries = idx->host_q;
+        l.ids = idx->host_ids;
+        l.d2 = d2_host ? idx->host_d2 : nullptr;
+        l.any_capped = idx->host_flag;
+        s = launch_dynamic(idx, l, st);
     }
-    for (cudaStream_t h : idx->host_st) {
-        const cudaError_t se = cudaStreamSynchronize(h);
-        if (e == cudaSuccess) e = se;
-    }
+    if (e == cudaSuccess && s == NSG_OK)
+        e = cudaMemcpyAsync(ids_host, idx->host_ids, sizeof(int) * nq * k, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && s == NSG_OK && d2_host)
+        e = cudaMemcpyAsync(d2_host, idx->host_d2, sizeof(float) * nq * k, cudaMemcpyDeviceToHost, st);
+    int capped = 0;
+    if (e == cudaSuccess && s == NSG_OK)
+        e = cudaMemcpyAsync(&capped, idx->host_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    const cudaError_t se = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = se;
     if (s) return s;
     if (e != cudaSuccess) return cuda_fail(e, "nsg_search_host");
-    int capped = 0;
-    NSG_CK(cudaMemcpyAsync(&capped, idx->host_flag, sizeof(int), cudaMemcpyDeviceToHost, idx->host_st[0]));
-    NSG_CK(cudaStreamSynchronize(idx->host_st[0]));
     return capped ? NSG_ESTEPCAP : NSG_OK;
 }
 

@@ -1,8 +1,8 @@
-"""Search on host buffers (nsg_search_host): the batch is cut into chunks
-that alternate over two streams, each chunk copied in, searched and copied
-back on its stream.  Results must equal the device-buffer search
-(nsg_search_ex) bit for bit -- whatever the chunking, page-locked or pageable
-host memory, with or without distances -- and the oracle on integer data."""
+"""Search on host buffers (nsg_search_host): queries copied into staging the
+index owns (grown on demand), one search launch, results copied back.
+Results must equal the device-buffer search (nsg_search_ex) bit for bit --
+for ragged batch sizes, page-locked or pageable host memory, with or without
+distances, after the staging has grown -- and the oracle on integer data."""
 import numpy as np
 import pytest
 import torch
