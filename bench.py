@@ -189,11 +189,12 @@ def kernel_source_hash(files=SEARCH_SOURCES):
 # the hash, and `traffic` is null until re-measured.
 NCU_TRAFFIC = {
     ("ae7f3d5fded47695", "sift", "u8", 150): (1_668_171_264 + 10_440_960) / 10_000,
+    ("ae7f3d5fded47695", "sift", "u8", 138): (1_539_700_992 + 10_233_600) / 10_000,
 }
 # the same for the MRNG edge selection of the build, per node, keyed by
 # (source hash, workload): profiles/prune_kernel_sift1m.md
 PRUNE_TRAFFIC = {
-    ("7c97dbc98864b866", "sift"): (18_417_009_408 + 135_907_328 + 15_953_364_992 + 113_341_440) / 1_000_000,
+    ("dc4dfdd243843fcb", "sift"): (18_540_747_008 + 134_831_616 + 16_068_677_120 + 113_730_048) / 1_000_000,
 }
 
 
