@@ -33,6 +33,9 @@
 
 // Unreached ids speculated per batch: larger batches run more searches in
 // parallel, smaller ones leave fewer earlier fix-ups to make a speculation stale.
+#ifndef NSG_CONNECT_U_WIDE8
+#define NSG_CONNECT_U_WIDE8 4  // rows in flight per warp, 513..1024-value rows
+#endif
 #ifndef NSG_CONNECT_BATCH
 #define NSG_CONNECT_BATCH 64
 #endif
@@ -379,8 +382,12 @@ cudaError_t run_connect(const ConnectLaunch &l, int out_host[4], cudaStream_t st
         cursor = (int64_t)h[1] + 1;
         if ((e = cudaMemsetAsync(dirty.p, 0, nwords * 4, st))) return e;
         NSG_DISPATCH_DP4(sa.dp4, {
-            auto spec = speculate_kernel<G_, V_, U_>;
-            auto commit = commit_kernel<G_, V_, U_>;
+            // one batch runs only 64 searches, so their latency, not the
+            // occupancy, sets the time: 513..1024-value rows keep more rows
+            // in flight than the search kernels do
+            constexpr int UC = V_ == 8 ? NSG_CONNECT_U_WIDE8 : U_;
+            auto spec = speculate_kernel<G_, V_, UC>;
+            auto commit = commit_kernel<G_, V_, UC>;
             if (!e) e = cudaFuncSetAttribute(spec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per_warp * wpb));
             if (!e) e = cudaFuncSetAttribute(commit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)per_warp);
             if (!e) {
