@@ -171,6 +171,29 @@ SEARCH_SOURCES = ("common.cuh", "search_core.cuh", "lowp.cuh", "search.cu")
 PRUNE_SOURCES = ("common.cuh", "search_core.cuh", "build.cu")
 
 
+def refine_L(pts, t, recall_at, qps_at):
+    """Smallest integer L between the last sweep point below recall t and the
+    first one at or above it that still reaches t (bisection, recall growing
+    with L), as a new sweep point; None when no L below that grid point does
+    or no grid point reaches t.  recall_at(L) and qps_at(L) measure one L."""
+    pts = sorted(pts, key=lambda p: p["L"])
+    above = [i for i, p in enumerate(pts) if p["recall10"] >= t]
+    if not above or above[0] == 0:
+        return None
+    lo, hi, hi_rec = pts[above[0] - 1]["L"], pts[above[0]]["L"], pts[above[0]]["recall10"]
+    grid_hi = hi
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        r = recall_at(mid)
+        if r >= t:
+            hi, hi_rec = mid, r
+        else:
+            lo = mid
+    if hi == grid_hi:
+        return None
+    return {"L": hi, "recall10": hi_rec, "qps": qps_at(hi), "refined": True}
+
+
 def kernel_source_hash(files=SEARCH_SOURCES):
     """Hash of a kernel's code with comments and blank lines removed, so that
     the hash changes with the code and not with its documentation."""
@@ -335,25 +358,7 @@ def main():
         return capi.nsg_recall(o["ids"][:, :10].contiguous(), gt, 10).sum().item() / (10.0 * nq)
 
     def refine(pts, prm, t):
-        """Smallest integer L between the last grid point below recall t and
-        the first one at or above it that still reaches t (bisection, recall
-        growing with L); the grid point itself when no smaller L does."""
-        pts = sorted(pts, key=lambda p: p["L"])
-        above = [i for i, p in enumerate(pts) if p["recall10"] >= t]
-        if not above or above[0] == 0:
-            return None
-        lo, hi, hi_rec = pts[above[0] - 1]["L"], pts[above[0]]["L"], pts[above[0]]["recall10"]
-        grid_hi = hi
-        while hi - lo > 1:
-            mid = (lo + hi) // 2
-            r = recall10(run(mid, prm))
-            if r >= t:
-                hi, hi_rec = mid, r
-            else:
-                lo = mid
-        if hi == grid_hi:
-            return None
-        return {"L": hi, "recall10": hi_rec, "qps": nq / (timed(prm, hi, 2) / 1e3), "refined": True}
+        return refine_L(pts, t, lambda L: recall10(run(L, prm)), lambda L: nq / (timed(prm, L, 2) / 1e3))
 
     # sweep L per form: recall@10 and a quick timing per point, then the
     # smallest L reaching each recall target between two grid points

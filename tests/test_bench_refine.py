@@ -1,0 +1,43 @@
+"""The bench's operating-point search (host logic, no GPU): between the last
+swept L below a recall target and the first one reaching it, bisection finds
+the smallest integer L that reaches the target, measuring recall only at the
+L it tries."""
+import bench
+
+
+def sweep(recall, Ls):
+    return [{"L": L, "recall10": recall(L), "qps": 1e6 / L} for L in Ls]
+
+
+def test_finds_smallest_L_reaching_target():
+    recall = lambda L: min(1.0, 0.8 + L / 1000.0)  # reaches 0.95 at L = 150
+    tried = []
+
+    def at(L):
+        tried.append(L)
+        return recall(L)
+
+    p = bench.refine_L(sweep(recall, [100, 125, 175, 200]), 0.95, at, lambda L: 1e6 / L)
+    assert p["L"] == 150 and p["recall10"] >= 0.95 and p["refined"]
+    assert all(125 < L < 175 for L in tried) and len(tried) <= 6
+
+
+def test_grid_point_already_smallest():
+    # no L below the grid point reaches the target: nothing new to add
+    recall = lambda L: 0.95 if L >= 125 else 0.90
+    assert bench.refine_L(sweep(recall, [100, 125, 150]), 0.95, recall, lambda L: 1.0) is None
+
+
+def test_target_unreached_or_reached_at_first_point():
+    recall = lambda L: 0.5
+    assert bench.refine_L(sweep(recall, [10, 20]), 0.95, recall, lambda L: 1.0) is None
+    recall = lambda L: 0.99
+    assert bench.refine_L(sweep(recall, [10, 20]), 0.95, recall, lambda L: 1.0) is None
+
+
+def test_result_is_measured_not_interpolated():
+    # a plateau: recall jumps at L = 133; the point returned carries the
+    # recall measured there
+    recall = lambda L: 0.96 if L >= 133 else 0.94
+    p = bench.refine_L(sweep(recall, [125, 150]), 0.95, recall, lambda L: 7.0)
+    assert p == {"L": 133, "recall10": 0.96, "qps": 7.0, "refined": True}
