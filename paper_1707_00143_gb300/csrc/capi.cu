@@ -10,7 +10,10 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <memory>
 #include <mutex>
+#include <new>
+#include <stdexcept>
 #include <vector>
 
 #include "kernels.h"
@@ -65,6 +68,19 @@ bool knn_force_scan() {
 nsg_status cuda_fail(cudaError_t e, const char *what) {
     std::snprintf(g_err, sizeof(g_err), "%s: %s", what, cudaGetErrorString(e));
     return NSG_ECUDA;
+}
+
+// Runs f() and turns a failed host allocation into NSG_ENOMEM, so that no
+// exception leaves the C ABI.
+template <class F>
+nsg_status host_guard(F &&f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc &) {
+        return NSG_ENOMEM;
+    } catch (const std::length_error &) {
+        return NSG_ENOMEM;
+    }
 }
 
 #define NSG_CK(x)                                                \
@@ -304,7 +320,7 @@ nsg_status collect_prune_all(const float *bp, int64_t n, int dp, const int *knn,
     return rc;
 }
 
-nsg_status finish_index(nsg_index *ix, cudaStream_t st) {
+nsg_status finish_index_body(nsg_index *ix, cudaStream_t st) {
     std::vector<int> deg((size_t)ix->n);
     NSG_CK(cudaMemcpyAsync(deg.data(), ix->deg, sizeof(int) * ix->n, cudaMemcpyDeviceToHost, st));
     NSG_CK(cudaStreamSynchronize(st));
@@ -319,6 +335,10 @@ nsg_status finish_index(nsg_index *ix, cudaStream_t st) {
     NSG_CK(cudaMalloc(reinterpret_cast<void **>(&ix->flag), 4 * sizeof(int)));
     NSG_CK(cudaMalloc(reinterpret_cast<void **>(&ix->work), kWorkSlots * sizeof(int)));
     return NSG_OK;
+}
+
+nsg_status finish_index(nsg_index *ix, cudaStream_t st) {
+    return host_guard([&] { return finish_index_body(ix, st); });
 }
 
 void destroy(nsg_index *ix) {
@@ -647,64 +667,66 @@ nsg_status nsg_build(const float *base_dev, int64_t n, int32_t d, int32_t K, int
 nsg_status nsg_index_from_graph(const float *base_dev, int64_t n, int32_t d, const int32_t *adj_dev,
                                 const int32_t *deg_dev, int32_t R, int32_t nav, void *stream,
                                 nsg_index **out) {
-    if (!out) return NSG_EINVAL;
-    *out = nullptr;
-    if (!base_dev || !adj_dev || n < 1 || n >= INT32_MAX || d < 1 || d > 4 * nsg::MAX_DP4_HOST ||
-        R < 1 || R > 1024 || nav < 0 || nav >= n)
-        return NSG_EINVAL;
-    cudaStream_t st = S(stream);
-    nsg_status s = check_ids(adj_dev, n * R, n, st);
-    if (s) return s;
-    nsg_index *ix = new (std::nothrow) nsg_index;
-    if (!ix) return NSG_ENOMEM;
-    ix->n = n;
-    ix->d = d;
-    ix->dp = round_up4(d);
-    ix->R = R;
-    ix->nav = nav;
-    DevBuf<float> base;
-    DevBuf<int> adj, deg;
-    s = padded_copy(base_dev, n, d, ix->dp, base, st);
-    cudaError_t e = cudaSuccess;
-    if (!s && (e = adj.alloc((size_t)n * R)) != cudaSuccess) s = cuda_fail(e, "alloc adj");
-    if (!s && (e = deg.alloc((size_t)n)) != cudaSuccess) s = cuda_fail(e, "alloc deg");
-    if (!s && (e = cudaMemcpyAsync(adj.p, adj_dev, sizeof(int) * n * R, cudaMemcpyDeviceToDevice, st)) !=
-                  cudaSuccess)
-        s = cuda_fail(e, "copy adj");
-    if (!s) {
-        if (deg_dev) {
-            e = cudaMemcpyAsync(deg.p, deg_dev, sizeof(int) * n, cudaMemcpyDeviceToDevice, st);
-            if (e != cudaSuccess) s = cuda_fail(e, "copy deg");
-        } else {
-            std::vector<int> h((size_t)n * R), dg((size_t)n);
-            e = cudaMemcpyAsync(h.data(), adj_dev, sizeof(int) * n * R, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e == cudaSuccess) {
-                for (int64_t v = 0; v < n; ++v) {
-                    int c = 0;
-                    while (c < R && h[v * R + c] >= 0) ++c;
-                    dg[v] = c;
-                }
-                e = cudaMemcpyAsync(deg.p, dg.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+    return host_guard([&]() -> nsg_status {
+        if (!out) return NSG_EINVAL;
+        *out = nullptr;
+        if (!base_dev || !adj_dev || n < 1 || n >= INT32_MAX || d < 1 || d > 4 * nsg::MAX_DP4_HOST ||
+            R < 1 || R > 1024 || nav < 0 || nav >= n)
+            return NSG_EINVAL;
+        cudaStream_t st = S(stream);
+        nsg_status s = check_ids(adj_dev, n * R, n, st);
+        if (s) return s;
+        nsg_index *ix = new (std::nothrow) nsg_index;
+        if (!ix) return NSG_ENOMEM;
+        ix->n = n;
+        ix->d = d;
+        ix->dp = round_up4(d);
+        ix->R = R;
+        ix->nav = nav;
+        DevBuf<float> base;
+        DevBuf<int> adj, deg;
+        s = padded_copy(base_dev, n, d, ix->dp, base, st);
+        cudaError_t e = cudaSuccess;
+        if (!s && (e = adj.alloc((size_t)n * R)) != cudaSuccess) s = cuda_fail(e, "alloc adj");
+        if (!s && (e = deg.alloc((size_t)n)) != cudaSuccess) s = cuda_fail(e, "alloc deg");
+        if (!s && (e = cudaMemcpyAsync(adj.p, adj_dev, sizeof(int) * n * R, cudaMemcpyDeviceToDevice, st)) !=
+                      cudaSuccess)
+            s = cuda_fail(e, "copy adj");
+        if (!s) {
+            if (deg_dev) {
+                e = cudaMemcpyAsync(deg.p, deg_dev, sizeof(int) * n, cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) s = cuda_fail(e, "copy deg");
+            } else {
+                std::vector<int> h((size_t)n * R), dg((size_t)n);
+                e = cudaMemcpyAsync(h.data(), adj_dev, sizeof(int) * n * R, cudaMemcpyDeviceToHost, st);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                if (e == cudaSuccess) {
+                    for (int64_t v = 0; v < n; ++v) {
+                        int c = 0;
+                        while (c < R && h[v * R + c] >= 0) ++c;
+                        dg[v] = c;
+                    }
+                    e = cudaMemcpyAsync(deg.p, dg.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                }
+                if (e != cudaSuccess) s = cuda_fail(e, "degrees");
             }
-            if (e != cudaSuccess) s = cuda_fail(e, "degrees");
         }
-    }
-    if (s) {
-        destroy(ix);
-        return s;
-    }
-    ix->base = base.release();
-    ix->adj = adj.release();
-    ix->deg = deg.release();
-    s = finish_index(ix, st);
-    if (s) {
-        destroy(ix);
-        return s;
-    }
-    *out = ix;
-    return NSG_OK;
+        if (s) {
+            destroy(ix);
+            return s;
+        }
+        ix->base = base.release();
+        ix->adj = adj.release();
+        ix->deg = deg.release();
+        s = finish_index(ix, st);
+        if (s) {
+            destroy(ix);
+            return s;
+        }
+        *out = ix;
+        return NSG_OK;
+    });
 }
 
 namespace {
@@ -879,7 +901,7 @@ void plan_destroy(nsg_plan *p) {
 
 // Validated batched launch with its visiting order (queries sorted by pool
 // size, largest first, so the longest searches start first) and work counter.
-nsg_status batched_setup(const nsg_index *idx, const float *queries_dev, int64_t nq, const int32_t *k_dev,
+nsg_status batched_setup_body(const nsg_index *idx, const float *queries_dev, int64_t nq, const int32_t *k_dev,
                          const int32_t *L_dev, int32_t kmax, int32_t Lmax, const nsg_search_params *params,
                          int32_t *ids_dev, float *d2_dev, int32_t *status_dev, nsg::SearchLaunch &l,
                          DevBuf<int> &order, DevBuf<int> &work, cudaStream_t st) {
@@ -901,6 +923,16 @@ nsg_status batched_setup(const nsg_index *idx, const float *queries_dev, int64_t
     l.order = order.p;
     l.work = work.p;
     return NSG_OK;
+}
+
+nsg_status batched_setup(const nsg_index *idx, const float *queries_dev, int64_t nq, const int32_t *k_dev,
+                         const int32_t *L_dev, int32_t kmax, int32_t Lmax, const nsg_search_params *params,
+                         int32_t *ids_dev, float *d2_dev, int32_t *status_dev, nsg::SearchLaunch &l,
+                         DevBuf<int> &order, DevBuf<int> &work, cudaStream_t st) {
+    return host_guard([&] {
+        return batched_setup_body(idx, queries_dev, nq, k_dev, L_dev, kmax, Lmax, params, ids_dev, d2_dev,
+                                  status_dev, l, order, work, st);
+    });
 }
 
 nsg_status batched_run(const nsg::SearchLaunch &l, cudaStream_t st) {
@@ -1197,67 +1229,77 @@ nsg_status nsg_index_graph(const nsg_index *idx, int32_t *adj_dev, int32_t *deg_
 static const char kMagic[8] = {'N', 'S', 'G', 'G', 'B', '3', '0', '0'};
 
 nsg_status nsg_save(const nsg_index *idx, const char *path) {
-    if (!idx || !path) return NSG_EINVAL;
-    const int64_t n = idx->n;
-    std::vector<int> deg((size_t)n), adj((size_t)n * idx->R);
-    std::vector<float> base((size_t)n * idx->d);
-    NSG_CK(cudaMemcpy(deg.data(), idx->deg, sizeof(int) * n, cudaMemcpyDeviceToHost));
-    NSG_CK(cudaMemcpy(adj.data(), idx->adj, sizeof(int) * n * idx->R, cudaMemcpyDeviceToHost));
-    NSG_CK(cudaMemcpy2D(base.data(), sizeof(float) * idx->d, idx->base, sizeof(float) * idx->dp,
-                        sizeof(float) * idx->d, n, cudaMemcpyDeviceToHost));
-    FILE *f = std::fopen(path, "wb");
-    if (!f) return NSG_EIO;
-    int32_t hdr[4] = {1, idx->d, idx->R, idx->nav};
-    bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, 4, 1, f) == 1 &&
-              std::fwrite(&n, 8, 1, f) == 1 && std::fwrite(&hdr[1], 4, 3, f) == 3 &&
-              std::fwrite(deg.data(), 4, deg.size(), f) == deg.size() &&
-              std::fwrite(adj.data(), 4, adj.size(), f) == adj.size() &&
-              std::fwrite(base.data(), 4, base.size(), f) == base.size();
-    ok = (std::fclose(f) == 0) && ok;
-    return ok ? NSG_OK : NSG_EIO;
+    return host_guard([&]() -> nsg_status {
+        if (!idx || !path) return NSG_EINVAL;
+        const int64_t n = idx->n;
+        std::vector<int> deg((size_t)n), adj((size_t)n * idx->R);
+        std::vector<float> base((size_t)n * idx->d);
+        NSG_CK(cudaMemcpy(deg.data(), idx->deg, sizeof(int) * n, cudaMemcpyDeviceToHost));
+        NSG_CK(cudaMemcpy(adj.data(), idx->adj, sizeof(int) * n * idx->R, cudaMemcpyDeviceToHost));
+        NSG_CK(cudaMemcpy2D(base.data(), sizeof(float) * idx->d, idx->base, sizeof(float) * idx->dp,
+                            sizeof(float) * idx->d, n, cudaMemcpyDeviceToHost));
+        FILE *f = std::fopen(path, "wb");
+        if (!f) return NSG_EIO;
+        int32_t hdr[4] = {1, idx->d, idx->R, idx->nav};
+        bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, 4, 1, f) == 1 &&
+                  std::fwrite(&n, 8, 1, f) == 1 && std::fwrite(&hdr[1], 4, 3, f) == 3 &&
+                  std::fwrite(deg.data(), 4, deg.size(), f) == deg.size() &&
+                  std::fwrite(adj.data(), 4, adj.size(), f) == adj.size() &&
+                  std::fwrite(base.data(), 4, base.size(), f) == base.size();
+        ok = (std::fclose(f) == 0) && ok;
+        return ok ? NSG_OK : NSG_EIO;
+    });
 }
 
 nsg_status nsg_load(const char *path, void *stream, nsg_index **out) {
-    if (!path || !out) return NSG_EINVAL;
-    *out = nullptr;
-    FILE *f = std::fopen(path, "rb");
-    if (!f) return NSG_EIO;
-    char magic[8];
-    int32_t ver = 0, hdr[3] = {0, 0, 0};
-    int64_t n = 0;
-    bool ok = std::fread(magic, 1, 8, f) == 8 && std::fread(&ver, 4, 1, f) == 1 &&
-              std::fread(&n, 8, 1, f) == 1 && std::fread(hdr, 4, 3, f) == 3;
-    if (!ok || std::memcmp(magic, kMagic, 8) != 0 || ver != 1 || n < 1 || n >= INT32_MAX || hdr[0] < 1 ||
-        hdr[0] > 4 * nsg::MAX_DP4_HOST || hdr[1] < 1 || hdr[1] > 1024 || hdr[2] < 0 || hdr[2] >= n) {
-        std::fclose(f);
-        return ok ? NSG_EFORMAT : NSG_EIO;
-    }
-    const int d = hdr[0], R = hdr[1], nav = hdr[2];
-    std::vector<int> deg((size_t)n), adj((size_t)n * R);
-    std::vector<float> base((size_t)n * d);
-    ok = std::fread(deg.data(), 4, deg.size(), f) == deg.size() &&
-         std::fread(adj.data(), 4, adj.size(), f) == adj.size() &&
-         std::fread(base.data(), 4, base.size(), f) == base.size();
-    std::fclose(f);
-    if (!ok) return NSG_EFORMAT;
-    for (int64_t v = 0; v < n; ++v) {
-        if (deg[v] < 0 || deg[v] > R) return NSG_EFORMAT;
-        for (int t = 0; t < R; ++t) {
-            int x = adj[v * R + t];
-            if (x < -1 || x >= n) return NSG_EFORMAT;
+    return host_guard([&]() -> nsg_status {
+        if (!path || !out) return NSG_EINVAL;
+        *out = nullptr;
+        std::unique_ptr<FILE, int (*)(FILE *)> f(std::fopen(path, "rb"), &std::fclose);
+        if (!f) return NSG_EIO;
+        char magic[8];
+        int32_t ver = 0, hdr[3] = {0, 0, 0};
+        int64_t n = 0;
+        const bool ok = std::fread(magic, 1, 8, f.get()) == 8 && std::fread(&ver, 4, 1, f.get()) == 1 &&
+                        std::fread(&n, 8, 1, f.get()) == 1 && std::fread(hdr, 4, 3, f.get()) == 3;
+        if (!ok) return NSG_EIO;
+        if (std::memcmp(magic, kMagic, 8) != 0 || ver != 1 || n < 1 || n >= INT32_MAX || hdr[0] < 1 ||
+            hdr[0] > 4 * nsg::MAX_DP4_HOST || hdr[1] < 1 || hdr[1] > 1024 || hdr[2] < 0 || hdr[2] >= n)
+            return NSG_EFORMAT;
+        const int d = hdr[0], R = hdr[1], nav = hdr[2];
+        // the header must describe exactly the bytes that follow it (checked
+        // before anything of that size is allocated)
+        const long at = std::ftell(f.get());
+        const int64_t want = (int64_t)at + 4 * (n + n * (int64_t)R + n * (int64_t)d);
+        if (at < 0 || std::fseek(f.get(), 0, SEEK_END) != 0 || (int64_t)std::ftell(f.get()) != want ||
+            std::fseek(f.get(), at, SEEK_SET) != 0)
+            return NSG_EFORMAT;
+        std::vector<int> deg((size_t)n), adj((size_t)n * R);
+        std::vector<float> base((size_t)n * d);
+        if (std::fread(deg.data(), 4, deg.size(), f.get()) != deg.size() ||
+            std::fread(adj.data(), 4, adj.size(), f.get()) != adj.size() ||
+            std::fread(base.data(), 4, base.size(), f.get()) != base.size())
+            return NSG_EFORMAT;
+        f.reset();
+        for (int64_t v = 0; v < n; ++v) {
+            if (deg[v] < 0 || deg[v] > R) return NSG_EFORMAT;
+            for (int t = 0; t < R; ++t) {
+                const int x = adj[v * R + t];
+                if (x < -1 || x >= n) return NSG_EFORMAT;
+            }
         }
-    }
-    cudaStream_t st = S(stream);
-    DevBuf<float> db;
-    DevBuf<int> da, dd;
-    NSG_CK(db.alloc(base.size()));
-    NSG_CK(da.alloc(adj.size()));
-    NSG_CK(dd.alloc(deg.size()));
-    NSG_CK(cudaMemcpyAsync(db.p, base.data(), 4 * base.size(), cudaMemcpyHostToDevice, st));
-    NSG_CK(cudaMemcpyAsync(da.p, adj.data(), 4 * adj.size(), cudaMemcpyHostToDevice, st));
-    NSG_CK(cudaMemcpyAsync(dd.p, deg.data(), 4 * deg.size(), cudaMemcpyHostToDevice, st));
-    NSG_CK(cudaStreamSynchronize(st));
-    return nsg_index_from_graph(db.p, n, d, da.p, dd.p, R, nav, stream, out);
+        cudaStream_t st = S(stream);
+        DevBuf<float> db;
+        DevBuf<int> da, dd;
+        NSG_CK(db.alloc(base.size()));
+        NSG_CK(da.alloc(adj.size()));
+        NSG_CK(dd.alloc(deg.size()));
+        NSG_CK(cudaMemcpyAsync(db.p, base.data(), 4 * base.size(), cudaMemcpyHostToDevice, st));
+        NSG_CK(cudaMemcpyAsync(da.p, adj.data(), 4 * adj.size(), cudaMemcpyHostToDevice, st));
+        NSG_CK(cudaMemcpyAsync(dd.p, deg.data(), 4 * deg.size(), cudaMemcpyHostToDevice, st));
+        NSG_CK(cudaStreamSynchronize(st));
+        return nsg_index_from_graph(db.p, n, d, da.p, dd.p, R, nav, stream, out);
+    });
 }
 
 void nsg_free(nsg_index *idx) { destroy(idx); }

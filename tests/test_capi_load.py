@@ -68,3 +68,42 @@ def test_validation_rejects_before_any_launch(libnsg):
     info = capi.IndexInfo()
     assert libnsg.nsg_index_info(None, C.byref(info)) == EINVAL
     libnsg.nsg_free(None)  # ignored
+
+
+def _index_file(path, n, d, R, nav=0, magic=b"NSGGB300", ver=1, deg=None, adj=None, extra=b""):
+    import numpy as np
+    deg = np.ones(n, np.int32) if deg is None else np.asarray(deg, np.int32)
+    adj = np.full((n, R), -1, np.int32) if adj is None else np.asarray(adj, np.int32)
+    with open(path, "wb") as f:
+        f.write(magic + np.int32(ver).tobytes() + np.int64(n).tobytes() + np.array([d, R, nav], np.int32).tobytes())
+        f.write(deg.tobytes() + adj.tobytes() + np.zeros((n, d), np.float32).tobytes() + extra)
+
+
+def test_load_rejects_bad_files_before_any_device_call(libnsg, tmp_path):
+    # every case fails in the header or content checks, before memory of the
+    # claimed size is allocated or the GPU is touched
+    from paper_1707_00143_gb300 import capi
+    out = C.c_void_p()
+    p = tmp_path / "idx.nsg"
+    assert libnsg.nsg_load(str(tmp_path / "missing").encode(), None, C.byref(out)) == capi.NSG_EIO
+    p.write_bytes(b"NSGGB3")  # short header
+    assert libnsg.nsg_load(str(p).encode(), None, C.byref(out)) == capi.NSG_EIO
+    _index_file(p, 3, 4, 2, magic=b"NOTANIDX")
+    assert libnsg.nsg_load(str(p).encode(), None, C.byref(out)) == capi.NSG_EFORMAT
+    _index_file(p, 3, 4, 2, ver=2)
+    assert libnsg.nsg_load(str(p).encode(), None, C.byref(out)) == capi.NSG_EFORMAT
+    # a header claiming 2^30 rows over a file of a few bytes
+    with open(p, "wb") as f:
+        import numpy as np
+        f.write(b"NSGGB300" + np.int32(1).tobytes() + np.int64(1 << 30).tobytes()
+                + np.array([128, 50, 0], np.int32).tobytes() + b"\0" * 64)
+    assert libnsg.nsg_load(str(p).encode(), None, C.byref(out)) == capi.NSG_EFORMAT
+    _index_file(p, 3, 4, 2, extra=b"\0\0\0\0")  # trailing bytes
+    assert libnsg.nsg_load(str(p).encode(), None, C.byref(out)) == capi.NSG_EFORMAT
+    _index_file(p, 3, 4, 2, adj=[[1, -1], [7, -1], [0, -1]])  # id out of range
+    assert libnsg.nsg_load(str(p).encode(), None, C.byref(out)) == capi.NSG_EFORMAT
+    _index_file(p, 3, 4, 2, deg=[1, 3, 1])  # degree above R
+    assert libnsg.nsg_load(str(p).encode(), None, C.byref(out)) == capi.NSG_EFORMAT
+    _index_file(p, 3, 4, 2, nav=3)  # navigating node out of range
+    assert libnsg.nsg_load(str(p).encode(), None, C.byref(out)) == capi.NSG_EFORMAT
+    assert out.value is None
