@@ -143,7 +143,7 @@ nsg_status nsg_centroid(const float *base_dev, int64_t n, int32_t d, double *cen
                         void *stream);
 
 /* ---------------------------------------------------------------------------
- * A3. Navigating node (Alg. 2; Section 3.4 step ii): Alg. 1 on the
+ * A3. Navigating node (Alg. 2; Section 3.5 step ii): Alg. 1 on the
  *   kNN graph from `start`, query = centroid, pool L; the navigating node is
  *   the first pool entry.  Distances to the centroid are FP64, summed over j
  *   in order without FMA contraction.  knn_ids_dev [n][K].
@@ -172,7 +172,7 @@ nsg_status nsg_navigate_noalloc(const float *base_dev, int64_t n, int32_t d, con
                                 int32_t *nav_host, void *stream);
 
 /* ---------------------------------------------------------------------------
- * A5. Search-and-collect (Alg. 2; Section 3.4 step iii; Fig. 4) for
+ * A5. Search-and-collect (Alg. 2; Section 3.5 step iii; Fig. 4) for
  *   nodes v0 .. v0+nv-1: Alg. 1 on the kNN graph from `nav` with query x_v
  *   and pool L; every node whose distance was computed, plus v's K kNN
  *   neighbours, minus v itself, sorted by key and cut to the C smallest.
@@ -198,7 +198,7 @@ nsg_status nsg_prune(const float *base_dev, int64_t n, int32_t d, const int32_t 
                      int64_t v0, int64_t nv, int32_t *adj_dev, int32_t *deg_dev, void *stream);
 
 /* ---------------------------------------------------------------------------
- * A7. Connectivity (Alg. 2; Section 3.4 step iv): reach from
+ * A7. Connectivity (Alg. 2; Section 3.5 step iv): reach from
  *   `nav` (BFS; the same reached set as the paper's DFS tree).  While a node
  *   is unreached: u = smallest unreached id; Alg. 1 on the current graph from
  *   nav with query x_u and pool L; the first result (key order) whose
@@ -238,7 +238,7 @@ nsg_status nsg_index_from_graph(const float *base_dev, int64_t n, int32_t d, con
                                 nsg_index **out);
 
 /* ---------------------------------------------------------------------------
- * A4. Search on NSG (Alg. 1 started at the navigating node, Section 3.5), one
+ * A4. Search on NSG (Alg. 1 started at the navigating node, Section 3.6), one
  *   warp per query: pool of L keys, expand the first unchecked entry, add its
  *   unvisited out-neighbours, keep the L smallest keys, stop when every entry
  *   is checked; return the first k.  queries_dev [nq][d] f32; ids_dev [nq][k]

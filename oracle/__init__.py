@@ -282,8 +282,45 @@ def search_random(adj, base, queries, k, L, count, seed, deg=None, nthreads=1):
     return ids, dist, ne, nd
 
 
+def partition_search(base, queries, part, K, L_build, R, Cap, k, L, seed=0, nthreads=None):
+    """Partition-and-merge search (Section 4.2): the base is split into
+    subsets (``part[i]`` = row i's subset), one NSG is built per subset (Alg. 2
+    on that subset's rows, ids local to it, kNN degree min(K, size - 1)),
+    every query runs Alg. 1 on every subset's NSG with pool L (returning
+    min(k, size) results), the local ids are mapped back to row ids, and the
+    union is cut to the k smallest keys (distance, row id).  Every subset
+    needs at least 2 rows.  Returns (ids [nq][k], d2 [nq][k]), padded with
+    -1 / +inf when the subsets hold fewer than k rows in all."""
+    base, queries = _f32(base), _f32(queries)
+    part = np.asarray(part)
+    if part.shape != (len(base),):
+        raise ValueError("part needs one subset id per base row")
+    if np.unique(part, return_counts=True)[1].min() < 2:
+        raise ValueError("every subset needs at least 2 rows")
+    nq = len(queries)
+    gids, dists = [], []
+    for p in np.unique(part):
+        rows = np.flatnonzero(part == p).astype(np.int32)
+        sub = base[rows]
+        g = build(sub, min(K, len(rows) - 1), L_build, R, Cap, seed=seed, nthreads=nthreads)
+        kp = min(k, len(rows))
+        ids, d2, _, _ = search(g["adj"], sub, g["nav"], queries, kp, max(L, kp), deg=g["deg"],
+                               nthreads=nthreads or nthreads_default())
+        gids.append(np.where(ids >= 0, rows[np.maximum(ids, 0)], -1).astype(np.int32))
+        dists.append(np.where(ids >= 0, d2, np.float32(np.inf)).astype(np.float32))
+    gid, dist = np.concatenate(gids, axis=1), np.concatenate(dists, axis=1)
+    out_ids = np.full((nq, k), -1, np.int32)
+    out_d2 = np.full((nq, k), np.inf, np.float32)
+    for q in range(nq):
+        # key order: distance, then row id; padding (+inf) sorts last
+        order = np.lexsort((np.where(gid[q] >= 0, gid[q], np.iinfo(np.int32).max), dist[q]))[:k]
+        m = len(order)
+        out_ids[q, :m], out_d2[q, :m] = gid[q, order], dist[q, order]
+    return out_ids, out_d2
+
+
 def mrng_naive(base):
-    """Naive MRNG construction (Section 3.3); adj [n][n-1] -1 padded, deg [n]."""
+    """Naive MRNG construction (Section 3.4); adj [n][n-1] -1 padded, deg [n]."""
     base = _f32(base)
     n, d = base.shape
     adj = np.empty((n, n - 1), np.int32)

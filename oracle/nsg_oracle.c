@@ -15,7 +15,7 @@
  *     the lower index breaks isosceles ties in the MRNG definition, Sec. 3.3);
  *   - Alg. 1 (Search-on-Graph), Alg. 2 (NSGbuild) with its centroid, navigating
  *     node, search-and-collect, MRNG edge selection and DFS-tree connectivity;
- *   - the naive MRNG construction of Section 3.3 and exact kNN by serial scan
+ *   - the naive MRNG construction of Section 3.4 and exact kNN by serial scan
  *     (Section 4.1.2, item 1).
  * Threads (pthreads) only split loops over independent queries / nodes /
  * column ranges whose results are merged by key, so every output is identical
@@ -27,7 +27,7 @@
  *   R2  S is a set: a node whose distance was computed once is never added
  *       again (identical to re-adding, see the proof in the design notes).
  *   R3  search-and-collect keeps every *visited* node (distance computed;
- *       Sec. 3.4 step iii-(2) and Fig. 4), plus all K kNN neighbours of v, minus
+ *       Sec. 3.5 step iii-(2) and Fig. 4), plus all K kNN neighbours of v, minus
  *       v itself; sorted by key and cut to the C smallest (C is a build cap).
  *   R4  edge selection: p is occluded when some kept r has dist(p,r) <
  *       dist(p,v) (r in the open lune of vp; Def. MRNG and Sec. 3.3); the first
@@ -412,7 +412,7 @@ static int32_t alg1(const graph *g, const metric *m, int32_t p, int32_t l, entry
 
 static int32_t graph_max_width(const graph *g) { return g->lazy ? g->lazy->k : g->width; }
 
-/* Search on a fixed graph (Alg. 1, Section 3.5): for each query, start at
+/* Search on a fixed graph (Alg. 1, Section 3.6): for each query, start at
  * `start`, pool size l, return the first k ids (-1 / +inf padded). */
 typedef struct {
     graph g;
@@ -798,7 +798,7 @@ int orc_build_naive(const float *base, int64_t n, int32_t d, int32_t K, int32_t 
     return rc;
 }
 
-/* Naive MRNG construction (Section 3.3): every other node is a candidate,
+/* Naive MRNG construction (Section 3.4): every other node is a candidate,
  * no degree cap.  adj is [n][n-1], -1 padded. */
 int orc_mrng_naive(const float *base, int64_t n, int32_t d, int32_t *adj, int32_t *deg) {
     if (!base || !adj || !deg || n < 2) return ORC_EINVAL;

@@ -57,7 +57,7 @@ cudaError_t launch_centroid(const float *base, int64_t n, int d, double *partial
 }
 
 // ---------------------------------------------------------------------------
-// Navigating node (Alg. 2; Section 3.4 ii): Alg. 1 on the kNN graph from `start`
+// Navigating node (Alg. 2; Section 3.5 ii): Alg. 1 on the kNN graph from `start`
 // toward the centroid, one warp.  Distances are FP64 sums over j in order with
 // explicitly rounded operations (no FMA), so they do not depend on the
 // compiler.  Lanes compute the distances of the new neighbours; lane 0 keeps

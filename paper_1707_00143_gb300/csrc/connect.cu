@@ -1,4 +1,4 @@
-// connect.cu -- the connectivity pass of Alg. 2 (Section 3.4 iv).
+// connect.cu -- the connectivity pass of Alg. 2 (Section 3.5 iv).
 //
 // Sequential definition (what the oracle computes): reach from the
 // navigating node; while some node is unreached, u = the smallest unreached

@@ -1,5 +1,5 @@
-// search.cu -- Alg. 1 for a batch of queries (search on NSG, Section 3.5) and
-// the per-node search-and-collect of Alg. 2 (Section 3.4 iii), one warp per unit.
+// search.cu -- Alg. 1 for a batch of queries (search on NSG, Section 3.6) and
+// the per-node search-and-collect of Alg. 2 (Section 3.5 iii), one warp per unit.
 #include <algorithm>
 #include <type_traits>
 

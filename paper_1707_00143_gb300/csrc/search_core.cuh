@@ -10,11 +10,11 @@
 // condition) or when the step cap is reached.
 //
 // The same routine serves
-//   * search on the NSG from the navigating node (Section 3.5),
-//   * search-and-collect on the kNN graph (Alg. 2, Section 3.4 iii): every computed
+//   * search on the NSG from the navigating node (Section 3.6),
+//   * search-and-collect on the kNN graph (Alg. 2, Section 3.5 iii): every computed
 //     key except the node itself is also merged into a collect list of the C
 //     smallest keys,
-//   * the connectivity pass (Alg. 2, Section 3.4 iv): speculative searches that also
+//   * the connectivity pass (Alg. 2, Section 3.5 iv): speculative searches that also
 //     log the ids they expand, and re-searches on a graph the same kernel is
 //     editing (plain coherent loads instead of the read-only path).
 #pragma once

@@ -143,3 +143,13 @@ def uneven_k_L(nq: int, seed: int, ks=(1, 10, 100), l_lo: int = 20, l_hi: int = 
     k = rng.choice(np.asarray(ks, dtype=np.int32), size=nq).astype(np.int32)
     L = rng.integers(l_lo, l_hi + 1, size=nq).astype(np.int32)
     return k, np.maximum(L, k).astype(np.int32)
+
+
+def even_partition(n: int, parts: int, seed: int) -> np.ndarray:
+    """Random even split of rows 0..n-1 into ``parts`` subsets (the partition
+    of Section 4.2's distributed search): a seeded permutation dealt out in
+    turn, so subset sizes differ by at most one.  Returns int32 [n] subset ids."""
+    rng = np.random.default_rng(seed)
+    part = np.empty(n, np.int32)
+    part[rng.permutation(n)] = np.arange(n, dtype=np.int64) % parts
+    return part
