@@ -283,7 +283,7 @@ def search_random(adj, base, queries, k, L, count, seed, deg=None, nthreads=1):
 
 
 def partition_search(base, queries, part, K, L_build, R, Cap, k, L, seed=0, nthreads=None):
-    """Partition-and-merge search (Section 4.2): the base is split into
+    """Partition-and-merge search (Sections 4.2, 4.3): the base is split into
     subsets (``part[i]`` = row i's subset), one NSG is built per subset (Alg. 2
     on that subset's rows, ids local to it, kNN degree min(K, size - 1)),
     every query runs Alg. 1 on every subset's NSG with pool L (returning

@@ -147,7 +147,7 @@ def uneven_k_L(nq: int, seed: int, ks=(1, 10, 100), l_lo: int = 20, l_hi: int = 
 
 def even_partition(n: int, parts: int, seed: int) -> np.ndarray:
     """Random even split of rows 0..n-1 into ``parts`` subsets (the partition
-    of Section 4.2's distributed search): a seeded permutation dealt out in
+    of the partitioned search of Sections 4.2 and 4.3): a seeded permutation dealt out in
     turn, so subset sizes differ by at most one.  Returns int32 [n] subset ids."""
     rng = np.random.default_rng(seed)
     part = np.empty(n, np.int32)

@@ -1,4 +1,4 @@
-"""Pins of the oracle's partition-and-merge search (Section 4.2: the base
+"""Pins of the oracle's partition-and-merge search (Sections 4.2, 4.3: the base
 split at random into subsets, one NSG per subset, every query searched on
 each, the results merged by key), against brute force, a hand-worked case
 and the one-subset identity."""
