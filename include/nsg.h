@@ -172,7 +172,7 @@ nsg_status nsg_navigate_noalloc(const float *base_dev, int64_t n, int32_t d, con
                                 int32_t *nav_host, void *stream);
 
 /* ---------------------------------------------------------------------------
- * A5. Search-and-collect (Alg. 2; Section 3.5 step iii; Fig. 4) for
+ * A5. Search-and-collect (Alg. 2; Section 3.5 step iii; Fig. 5) for
  *   nodes v0 .. v0+nv-1: Alg. 1 on the kNN graph from `nav` with query x_v
  *   and pool L; every node whose distance was computed, plus v's K kNN
  *   neighbours, minus v itself, sorted by key and cut to the C smallest.

@@ -27,7 +27,7 @@
  *   R2  S is a set: a node whose distance was computed once is never added
  *       again (identical to re-adding, see the proof in the design notes).
  *   R3  search-and-collect keeps every *visited* node (distance computed;
- *       Sec. 3.5 step iii-(2) and Fig. 4), plus all K kNN neighbours of v, minus
+ *       Sec. 3.5 step iii-(2) and Fig. 5), plus all K kNN neighbours of v, minus
  *       v itself; sorted by key and cut to the C smallest (C is a build cap).
  *   R4  edge selection: p is occluded when some kept r has dist(p,r) <
  *       dist(p,v) (r in the open lune of vp; Def. MRNG and Sec. 3.3); the first
