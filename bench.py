@@ -415,7 +415,9 @@ def main():
                           "queries": qs_n, "k": 10, "exact_copy": bool(info["has_" + name] == 2)}
 
     # algorithmic bytes at the chosen point: unique distance and expansion counts
-    big = capi.SearchParams(0, 16384, prm.precision, 0, prm.rerank)
+    # (the chosen form's parameters, learned stop included, with an exact visited set)
+    big = capi.SearchParams.from_buffer_copy(prm)
+    big.hash_slots, big.warps_per_cta = 16384, 0
     kc = kq(L)
     cnt = idx.search_ex(qt, kc, L, params=big)
     n_dist = cnt["n_dist"].to(torch.int64).sum().item()
