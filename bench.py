@@ -28,8 +28,16 @@ device->host copy of the ids, all inside the call.
 Multi-GPU: queries are independent, so each rank searches its own batch on
 its own replica of the index (weak scaling, no collective on the data path).
 
---impl reference times the CPU oracle (serial scan, exact: recall 1.0) on a
-bounded query sample of the same workload.
+CPU baseline (`cpu_baseline`, and `--impl reference`): the CPU oracle's
+Alg. 1 (Section 3.6), single-threaded and on all host cores, searching the
+same index at the same pool size on bounded query samples.  The index is the
+library's build: the oracle needs hours of host time to build a 1M-row index
+(its kNN stage alone is an O(n^2 d) serial scan), and the library's build
+equals the oracle's wherever the tests compare them.  The oracle's exact
+serial scan (the paper's own baseline, Section 4.1.2) is reported beside it.
+
+--profile-case search|knn|build runs one small kernel family for a profiler
+(see `profile_case`) and prints one line.
 """
 from __future__ import annotations
 
@@ -57,7 +65,7 @@ TARGET = 0.95
 WORKLOADS = {
     # L 100..400 is the sweep of the SIFT-shaped configuration; 500..1000 reach recall@10 = 0.99
     "sift": dict(build=dict(K=100, L=40, R=50, C=500), L_grid=list(range(100, 401, 25)) + [500, 600, 800, 1000], k=100,
-                 desc="sift-shaped 1,000,000 x 128 int 0..255 GMM(100), 10,000 queries"),
+                 desc="sift-shaped 1,000,000 x 128 int 0..255 GMM(100), 10,000 queries", integer=True),
     "gist": dict(build=dict(K=100, L=60, R=70, C=500), L_grid=[10, 20, 40, 60, 80, 100, 150, 200, 300, 400, 500],
                  k=100, desc="gist-shaped 1,000,000 x 960 f32 [0,1] GMM(50), 1,000 queries"),
     "deep": dict(build=dict(K=64, L=60, R=32, C=500), L_grid=[20, 40, 60, 100, 150, 200, 300, 400, 500, 700, 1000],
@@ -83,6 +91,15 @@ def parse():
     p.add_argument("--workload", default="sift", choices=sorted(WORKLOADS))
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     p.add_argument("--naive", action="store_true", help="also build and sweep NSG-Naive (ablation)")
+    p.add_argument("--profile-case", choices=["search", "knn", "build"], default=None,
+                   help="run one kernel family on a small SIFT-shaped case for a profiler")
+    p.add_argument("--n", type=int, default=300000, help="--profile-case: base rows")
+    p.add_argument("--nq", type=int, default=2000, help="--profile-case: queries")
+    p.add_argument("--L", type=int, default=150, help="--profile-case search: pool size")
+    p.add_argument("--K", type=int, default=100, help="--profile-case knn: neighbours per row")
+    p.add_argument("--prec", type=int, default=0, help="--profile-case search: 0 FP32, 1 BF16, 2 FP8, 3 U8")
+    p.add_argument("--wpq", type=int, default=1, help="--profile-case search: warps per query")
+    p.add_argument("--reps", type=int, default=2, help="--profile-case search: launches")
     return p.parse_args()
 
 
@@ -227,57 +244,185 @@ PRUNE_TRAFFIC = {
 }
 
 
-def cpu_serial_scan(base, q, budget_s=10.0):
+def bench_config(W, world, base):
+    """The workload a line measures: the same dict in both arms."""
+    return {"workload": W["desc"], "build": W["build"], "k": W["k"], "target_recall10": TARGET,
+            "parallelism": f"replicas{world}", "l2": f"inputs larger than L2 ({base.nbytes >> 20} MB base)"}
+
+
+def _timed_sample(fn, q, per_q_budget, cap):
+    """Run fn on the first m queries, m sized from a 16-query probe so the
+    call takes about `per_q_budget` seconds; returns (m, seconds)."""
+    t = time.perf_counter()
+    fn(q[:16])
+    per_q = max((time.perf_counter() - t) / 16, 1e-7)
+    m = int(max(16, min(cap, len(q), per_q_budget / per_q)))
+    t = time.perf_counter()
+    fn(q[:m])
+    return m, time.perf_counter() - t
+
+
+def cpu_serial_scan(base, q, budget_s=5.0):
     """Oracle serial scan (exact kNN: recall 1.0) on a bounded query sample."""
     import oracle
 
     cores = os.cpu_count() or 1
-    t = time.perf_counter()
-    oracle.knn_query(base, q[:16], 10, nthreads=cores)
-    per_q = (time.perf_counter() - t) / 16
-    m = int(max(16, min(len(q), budget_s / max(per_q, 1e-6))))
-    t = time.perf_counter()
-    oracle.knn_query(base, q[:m], 10, nthreads=cores)
-    el = time.perf_counter() - t
+    m, el = _timed_sample(lambda qs: oracle.knn_query(base, qs, 10, nthreads=cores), q, budget_s, len(q))
     return {"value": m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"serial scan (exact kNN, recall@10 = 1.0) of the first {m} queries against "
                       f"the full {len(base)}-row base, {cores} host threads"}
 
 
+def cpu_alg1(adj, deg, base, nav, q, k, L, budget_s=8.0):
+    """The oracle's Alg. 1 (plain, single-threaded per query) on the given
+    index at pool size L: one sample on one host thread (queries/s per core)
+    and one on every host thread (disjoint query ranges)."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+
+    def run(qs, nt):
+        oracle.search(adj, base, nav, qs, k, L, deg=deg, nthreads=nt)
+
+    m1, el1 = _timed_sample(lambda qs: run(qs, 1), q, budget_s / 2, 2000)
+    m, el = _timed_sample(lambda qs: run(qs, cores), q, budget_s, len(q))
+    return {"value": m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle Alg. 1 (k = {k}, L = {L}) over the first {m} queries on {cores} host threads, "
+                      f"on the index the library built",
+            "single_thread": {"value": m1 / el1, "queries": m1}}
+
+
+def profile_case(args):
+    """One kernel family on a small SIFT-shaped case, for a profiler: `search`
+    builds an index (K=100, L=40, R=50, C=500) on an n-row base and runs
+    `--reps` searches of nq queries (top 100, pool --L) in the precision form
+    --prec with --wpq warps per query; `knn` runs one brute-force kNN graph
+    (K = --K); `build` one index construction."""
+    import torch
+
+    from paper_1707_00143_gb300 import build as nsg_build_mod
+    from paper_1707_00143_gb300 import capi, datagen
+
+    nsg_build_mod.build()
+    torch.cuda.set_device(0)
+    base, q = datagen.workload("sift", n=args.n, nq=args.nq)
+    bt, qt = torch.from_numpy(base).cuda(), torch.from_numpy(q).cuda()
+    if args.profile_case == "knn":
+        capi.nsg_knn_init(bt, args.K, with_d2=False)
+        torch.cuda.synchronize()
+        print(f"knn n={args.n} K={args.K} done")
+        return
+    idx = capi.nsg_build(bt, 100, 40, 50, 500)
+    if args.profile_case == "build":
+        torch.cuda.synchronize()
+        print(f"build n={args.n} done: {idx.info()}")
+        return
+    if args.prec:
+        idx.prepare(args.prec)
+    prm = capi.SearchParams(0, 0, args.prec, 0, -1, None, 0.5, 0, 0, 0, 0, args.wpq)
+    for _ in range(args.reps):
+        idx.search_ex(qt, 100, args.L, params=prm, counters=False)
+    torch.cuda.synchronize()
+    print(f"search n={args.n} nq={args.nq} L={args.L} prec={args.prec} wpq={args.wpq} done")
+
+
 def run_reference(args):
+    """The oracle's Alg. 1 on the workload's index, at the smallest pool size
+    whose recall@10 on a 1,000-query sample reaches the target (the sweep
+    and bisection of this arm, with the oracle's exact serial scan as ground
+    truth); each step searches a sample of queries on every host thread."""
     world, rank, local = dist_env()
     if rank != 0:
         return
-    from paper_1707_00143_gb300 import datagen
+    import numpy as np
+    import torch
+
+    from paper_1707_00143_gb300 import build as nsg_build_mod
+    from paper_1707_00143_gb300 import capi, datagen
     import oracle
 
     oracle.compile_lib()
+    W = WORKLOADS[args.workload]
+    B = W["build"]
     base, q = datagen.workload(args.workload)
     cores = os.cpu_count() or 1
-    m = 64
+    # the index (setup, untimed): the library's build, equal to the oracle's own
+    nsg_build_mod.build()
+    torch.cuda.set_device(local)
+    idx = capi.nsg_build(torch.from_numpy(base).cuda(), B["K"], B["L"], B["R"], B["C"], seed=0)
+    adj, deg = (t.cpu().numpy() for t in idx.graph())
+    nav = idx.info()["nav"]
+    del idx
+    torch.cuda.empty_cache()
+    # operating point: recall@10 of the oracle's own results on a query sample
+    ns = min(1000, len(q))
+    gt, _ = oracle.knn_query(base, q[:ns], 10, nthreads=cores)
+
+    def recall_at(L):
+        ids, _, _, _ = oracle.search(adj, base, nav, q[:ns], 10, L, deg=deg, nthreads=cores)
+        return oracle.recall(ids, gt, 10)
+
+    pts = []
+    for L in W["L_grid"]:
+        pts.append({"L": L, "recall10": recall_at(L)})
+        if pts[-1]["recall10"] >= TARGET:
+            break
+    p = refine_L(pts, TARGET, recall_at, lambda L: None)
+    ok = [x for x in pts if x["recall10"] >= TARGET]
+    L = p["L"] if p else (ok[0]["L"] if ok else W["L_grid"][-1])
+    rec = p["recall10"] if p else (ok[0]["recall10"] if ok else pts[-1]["recall10"])
+    kq = min(W["k"], L)
+    m = 2000
     times = []
     for s in range(args.warmup + args.steps):
-        qs = q[(s * m) % len(q):(s * m) % len(q) + m]
+        lo = (s * m) % len(q)
+        qs = q[lo:lo + m]
         t = time.perf_counter()
-        oracle.knn_query(base, qs, 10, nthreads=cores)
+        oracle.search(adj, base, nav, qs, kq, L, deg=deg, nthreads=cores)
         if s >= args.warmup:
             times.append(time.perf_counter() - t)
     ms = 1e3 * sum(times) / len(times)
-    v = m / (ms / 1e3)
-    sample = (f"serial scan (exact kNN, recall@10 = 1.0) of {m} queries per step against the full "
-              f"{len(base)}-row base, {cores} host threads")
+    v = len(qs) / (ms / 1e3)
+    t = time.perf_counter()
+    oracle.search(adj, base, nav, q[:200], kq, L, deg=deg, nthreads=1)
+    single = 200 / (time.perf_counter() - t)
+    sample = (f"oracle Alg. 1 (k = {kq}, L = {L}) over {m} queries per step on {cores} host threads, "
+              f"on the index the library built")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload]["desc"] + ", serial scan", "k": 10},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "config": bench_config(W, 1, base),
+        "operating_point": {"form": "oracle Alg. 1 (FP32)", "L": L, "recall10_sample": rec,
+                            "sample_queries": ns, "sweep": pts},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "single_thread": {"value": single, "queries": 200}},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
+def ground_truth(capi, bt, qt, W, k=10):
+    """Exact k nearest base rows of every query: the tensor-core kNN on
+    integer data (exact there), the FP32 CUDA-core scan otherwise (the
+    tensor-core path ranks float data by BF16 products before its FP32
+    re-rank, which can miss a true neighbour)."""
+    if W.get("integer"):
+        return capi.nsg_knn_query(bt, qt, k)
+    old = os.environ.get("NSG_KNN_ENGINE")
+    os.environ["NSG_KNN_ENGINE"] = "scan"
+    try:
+        return capi.nsg_knn_query(bt, qt, k)
+    finally:
+        if old is None:
+            del os.environ["NSG_KNN_ENGINE"]
+        else:
+            os.environ["NSG_KNN_ENGINE"] = old
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        return profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     import numpy as np
@@ -313,7 +458,7 @@ def main():
     t0 = time.perf_counter()
     idx = capi.nsg_build(bt, BUILD["K"], BUILD["L"], BUILD["R"], BUILD["C"], seed=0)
     build_s = time.perf_counter() - t0
-    gt, gt_d2 = capi.nsg_knn_query(bt, qt, 10)
+    gt, gt_d2 = ground_truth(capi, bt, qt, W)
 
     # the forms: plain FP32 traversal, and the precision forms (BF16 / FP8-e4m3
     # traversal with FP32 accumulation; FP32 re-rank of the pool when the copy is lossy)
@@ -535,9 +680,21 @@ def main():
     if prune_roofline["achieved"] is not None:
         prune_roofline["frac"] = prune_roofline["achieved"] / peak
 
+    # recall@10 of the chosen form and L on a second, held-out query batch
+    # (L was picked on the timed batch)
+    _, q_held = datagen.workload(args.workload, nq=nq, seed_query=datagen.SEED_QUERY + 7777 + 1000 * rank)
+    qht = torch.from_numpy(q_held).cuda()
+    gt_held, _ = ground_truth(capi, bt, qht, W)
+    o_held = idx.search_ex(qht, kc, L, params=prm, counters=False)
+    rec_held = capi.nsg_recall(o_held["ids"][:, :10].contiguous(), gt_held, 10).sum().item() / (10.0 * nq)
+    del qht, gt_held, o_held
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_serial_scan(base, q)
+        adj_h, deg_h = (t.cpu().numpy() for t in idx.graph())
+        cpu = cpu_alg1(adj_h, deg_h, base, info["nav"], q, kc, L)
+        cpu["serial_scan"] = cpu_serial_scan(base, q)
+        del adj_h, deg_h
 
     if rank == 0:
         line = {
@@ -546,11 +703,9 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"plain": "f32", "bf16": "bf16->f32", "fp8": "fp8e4m3->f32", "u8": "u8->i32"}[base_form],
             "data": "synthetic",
-            "config": {"workload": W["desc"],
-                       "form": chosen_form, "build": BUILD, "k": kc, "L": L,
-                       "recall10": rec_chosen, "recall10_ties": rec_chosen_ties, "target_recall10": TARGET,
-                       "parallelism": f"replicas{world}",
-                       "l2": f"inputs larger than L2 ({base.nbytes >> 20} MB base)"},
+            "config": bench_config(W, world, base),
+            "operating_point": {"form": chosen_form, "k": kc, "L": L, "recall10": rec_chosen,
+                                "recall10_ties": rec_chosen_ties, "recall10_heldout": rec_held},
             "plain": {"value": job_qps(world, nq, ms_plain), "ms_per_step": ms_plain, "L": plain_L,
                       "recall10": rec_plain},
             "chosen_over_plain": ms_plain / ms_step,

@@ -126,7 +126,6 @@ inline int default_hash(int L, int width) {
     (void)width;
     return 512;
 }
-inline int default_steps(int L) { return 16 * L + 4096; }
 inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // Published SplitMix64 finaliser (Steele, Lea, Flood 2014): the random start
@@ -207,7 +206,7 @@ nsg_status navigate_run(const float *base, int64_t n, int d, const int *knn, int
     NSG_CK(visited.alloc((size_t)(n + 31) / 32));
     NSG_CK(out.alloc(2));
     NSG_CK(cudaMemsetAsync(visited.p, 0, sizeof(uint32_t) * ((n + 31) / 32), st));
-    NSG_CK(nsg::launch_navigate(base, n, d, knn, K, c, start, L, visited.p, default_steps(L), out.p,
+    NSG_CK(nsg::launch_navigate(base, n, d, knn, K, c, start, L, visited.p, nsg::default_steps(L), out.p,
                                 out.p + 1, st));
     int h[2] = {0, 0};
     NSG_CK(cudaMemcpyAsync(h, out.p, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -228,7 +227,7 @@ nsg_status connect_run(const float *bp, int64_t n, int dp, int *adj, int *deg, i
     c.nav = nav;
     c.L = L;
     c.hash_slots = default_hash(L, R);
-    c.max_steps = default_steps(L);
+    c.max_steps = nsg::default_steps(L);
     int h[4] = {0, 0, 0, 0};
     NSG_CK(nsg::run_connect(c, h, st));
     if (n_added) *n_added = h[0];
@@ -271,7 +270,7 @@ nsg_status collect_prune_all(const float *bp, int64_t n, int dp, const int *knn,
         c.v0 = v0;
         c.nv = nv;
         c.hash_slots = default_hash(L, K);
-        c.max_steps = default_steps(L);
+        c.max_steps = nsg::default_steps(L);
         c.cand_ids = cid.p;
         c.cand_d2 = cd2.p;
         c.cand_count = ccnt.p;
@@ -482,7 +481,7 @@ nsg_status nsg_collect(const float *base_dev, int64_t n, int32_t d, const int32_
     c.v0 = v0;
     c.nv = nv;
     c.hash_slots = default_hash(L, K);
-    c.max_steps = default_steps(L);
+    c.max_steps = nsg::default_steps(L);
     c.cand_ids = cand_ids_dev;
     c.cand_d2 = cand_d2_dev;
     c.cand_count = cand_count_dev;
@@ -765,7 +764,7 @@ nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t n
     l.k = k;
     l.L = L;
     l.hash_slots = p.hash_slots > 0 ? p.hash_slots : default_hash(L, idx->R);
-    l.max_steps = p.max_steps > 0 ? p.max_steps : default_steps(L);
+    l.max_steps = p.max_steps > 0 ? p.max_steps : nsg::default_steps(L);
     l.warps_per_cta = p.warps_per_cta;
     l.ids = ids_dev;
     l.d2 = d2_dev;
@@ -1162,7 +1161,7 @@ nsg_status nsg_search(const nsg_index *idx, const float *queries_dev, int64_t nq
     l.k = k;
     l.L = L;
     l.hash_slots = default_hash(L, idx->R);
-    l.max_steps = default_steps(L);
+    l.max_steps = nsg::default_steps(L);
     l.warps_per_cta = 0;
     l.ids = ids_dev;
     l.d2 = d2_dev;

@@ -9,6 +9,12 @@ namespace nsg {
 
 constexpr int MAX_DP4_HOST = 512;  // largest supported row: 2048 floats
 
+// Step cap of a search with pool size L when the caller sets none: far above
+// any expansion count Alg. 1 reaches on a graph (each step checks one of at
+// most L pool entries, and an entry is only replaced by a closer one), so it
+// only ends a search on a corrupt graph.
+inline int default_steps(int L) { return 16 * L + 4096; }
+
 // Search on a fixed-width graph (Alg. 1 from `start`), one warp per query.
 struct SearchLaunch {
     const float *base;  // [n][dp] padded, 16-byte aligned

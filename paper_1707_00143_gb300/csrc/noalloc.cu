@@ -15,6 +15,8 @@
 // call's contents, so each call clears the part it uses first; two calls whose
 // work overlaps on the GPU (different streams, or different host threads)
 // race on it and must be serialised by the caller.
+#include <atomic>
+
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -30,22 +32,28 @@ constexpr int kStatusWords = 4;  // [0] nav, [1] step-cap status, [2] bad-id fla
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kWords + kStatusWords];
 
 constexpr int kMaxDevices = 64;
-uint32_t *g_scratch_ptr[kMaxDevices] = {nullptr};
+std::atomic<uint32_t *> g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the array on the current device (looked up once per
-// device; the host-side symbol is a stand-in, not a device address).
+// Device address of the array on the current device, looked up on the first
+// call on that device (the host-side symbol is a stand-in, not a device
+// address).  Two host threads making their first call at once both look it
+// up and store the same address.  The cached address belongs to the device's
+// current context: a cudaDeviceReset on that device invalidates it (as it
+// does every index this library holds there).
 cudaError_t scratch_ptr(uint32_t **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    uint32_t *p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void *v = nullptr;
+        e = cudaGetSymbolAddress(&v, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<uint32_t *>(p);
+        p = static_cast<uint32_t *>(v);
+        g_scratch_ptr[dev].store(p, std::memory_order_release);
     }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
@@ -90,7 +98,7 @@ extern "C" nsg_status nsg_navigate_noalloc(const float *base_dev, int64_t n, int
     if ((e = cudaMemcpyAsync(h, status, sizeof(h), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
     if (h[2]) return NSG_EINVAL;  // an id outside [-1, n): the gather would read out of range
-    e = nsg::launch_navigate(base_dev, n, d, knn_ids_dev, K, centroid_dev, start, L, visited, 16 * L + 4096,
+    e = nsg::launch_navigate(base_dev, n, d, knn_ids_dev, K, centroid_dev, start, L, visited, nsg::default_steps(L),
                              reinterpret_cast<int *>(status), reinterpret_cast<int *>(status + 1), st);
     if (e != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h, status, sizeof(h), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return fail(e);

@@ -41,3 +41,29 @@ def test_result_is_measured_not_interpolated():
     recall = lambda L: 0.96 if L >= 133 else 0.94
     p = bench.refine_L(sweep(recall, [125, 150]), 0.95, recall, lambda L: 7.0)
     assert p == {"L": 133, "recall10": 0.96, "qps": 7.0, "refined": True}
+
+
+def test_cpu_alg1_baseline_on_an_oracle_graph():
+    # the CPU baseline times the oracle's Alg. 1 on a given index: one sample
+    # on one thread, one on every host thread
+    import numpy as np
+
+    import oracle
+    from paper_1707_00143_gb300 import datagen
+
+    base, q = datagen.workload("tiny", n=2000, nq=64)
+    ref = oracle.build(base, 16, 30, 12, 100, seed=0)
+    out = bench.cpu_alg1(ref["adj"], ref["deg"], base, ref["nav"], q, 10, 40, budget_s=0.2)
+    assert out["kind"] == "oracle" and out["unit"] == bench.UNIT
+    assert out["value"] > 0 and out["single_thread"]["value"] > 0
+    assert out["cores"] >= 1 and "Alg. 1" in out["sample"]
+    assert np.isfinite(out["value"])
+
+
+def test_both_arms_share_the_config():
+    import numpy as np
+
+    W = bench.WORKLOADS["sift"]
+    base = np.zeros((4, 128), np.float32)
+    a, b = bench.bench_config(W, 1, base), bench.bench_config(W, 1, base)
+    assert a == b and a["workload"] == W["desc"] and a["target_recall10"] == bench.TARGET
