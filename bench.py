@@ -66,14 +66,18 @@ WORKLOADS = {
     # L 100..400 is the sweep of the SIFT-shaped configuration; 500..1000 reach recall@10 = 0.99
     "sift": dict(build=dict(K=100, L=40, R=50, C=500), L_grid=list(range(100, 401, 25)) + [500, 600, 800, 1000], k=100,
                  desc="sift-shaped 1,000,000 x 128 int 0..255 GMM(100), 10,000 queries", integer=True),
-    "gist": dict(build=dict(K=100, L=60, R=70, C=500), L_grid=[10, 20, 40, 60, 80, 100, 150, 200, 300, 400, 500],
+    "gist": dict(build=dict(K=100, L=60, R=70, C=500),
+                 L_grid=[10, 20, 40, 60, 80, 100, 150, 200, 300, 400, 500, 1000, 2000, 4000],
                  k=100, desc="gist-shaped 1,000,000 x 960 f32 [0,1] GMM(50), 1,000 queries"),
-    "deep": dict(build=dict(K=64, L=60, R=32, C=500), L_grid=[20, 40, 60, 100, 150, 200, 300, 400, 500, 700, 1000],
+    "deep": dict(build=dict(K=64, L=60, R=32, C=500),
+                 L_grid=[20, 40, 60, 100, 150, 200, 300, 400, 500, 700, 1000, 2000, 4000],
                  k=100, desc="deep-shaped 10,000,000 x 96 f32 unit-norm GMM(1000), 100,000 queries"),
     # the paper's own synthetic sets (Table 1); R = 220 is the maximum out-degree it reports for them
-    "rand4m": dict(build=dict(K=100, L=60, R=220, C=500), L_grid=[20, 40, 60, 100, 150, 200, 300, 400, 500, 700, 1000],
+    "rand4m": dict(build=dict(K=100, L=60, R=220, C=500),
+                   L_grid=[20, 40, 60, 100, 150, 200, 300, 400, 500, 700, 1000, 2000, 4000],
                    k=100, desc="RAND4M: 4,000,000 x 128 i.i.d. U(0,1), 10,000 queries"),
-    "gauss5m": dict(build=dict(K=100, L=60, R=220, C=500), L_grid=[20, 40, 60, 100, 150, 200, 300, 400, 500, 700, 1000],
+    "gauss5m": dict(build=dict(K=100, L=60, R=220, C=500),
+                    L_grid=[20, 40, 60, 100, 150, 200, 300, 400, 500, 700, 1000, 2000, 4000],
                     k=100, desc="GAUSS5M: 5,000,000 x 128 i.i.d. N(0,3), 10,000 queries"),
 }
 STOP_TRACE_LS, STOP_TRACE_CAP, STOP_ITERS = (100, 200, 400), 1024, 300
@@ -91,6 +95,8 @@ def parse():
     p.add_argument("--workload", default="sift", choices=sorted(WORKLOADS))
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     p.add_argument("--naive", action="store_true", help="also build and sweep NSG-Naive (ablation)")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the partition-and-merge and nn-descent legs")
     p.add_argument("--profile-case", choices=["search", "knn", "build"], default=None,
                    help="run one kernel family on a small SIFT-shaped case for a profiler")
     p.add_argument("--n", type=int, default=300000, help="--profile-case: base rows")
@@ -190,7 +196,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sm)}
 
 
-SEARCH_SOURCES = ("common.cuh", "search_core.cuh", "lowp.cuh", "search.cu")
+SEARCH_SOURCES = ("common.cuh", "search_core.cuh", "lowp.cuh", "search_kern.cuh", "search.cu")
 PRUNE_SOURCES = ("common.cuh", "search_core.cuh", "build.cu")
 
 
@@ -399,6 +405,103 @@ def run_reference(args):
                          "single_thread": {"value": single, "queries": 200}},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def sweep_point(L_grid, run_recall, run_ms, nq, target=TARGET):
+    """Grid sweep + bisection to the smallest L reaching `target`; returns
+    (point with L, recall10, qps | None, sweep points)."""
+    pts = []
+    for L in L_grid:
+        pts.append({"L": L, "recall10": run_recall(L), "qps": nq / (run_ms(L) / 1e3)})
+        if pts[-1]["recall10"] >= target:
+            break
+    p = refine_L(pts, target, run_recall, lambda L: nq / (run_ms(L) / 1e3))
+    if p is not None:
+        pts.append(p)
+        pts.sort(key=lambda x: x["L"])
+    ok = [x for x in pts if x["recall10"] >= target]
+    return (max(ok, key=lambda x: x["qps"]) if ok else None), pts
+
+
+def extra_legs(capi, datagen, bt, qt, gt, base, W, forms, chosen_form, nq, kq, recall10, ev0, ev1, st, args):
+    """Partition-and-merge search (Sections 4.2, 4.3) at P = 4 and 8 subsets and
+    a build whose kNN stage is nn-descent (Sec. 3.5 (ii)): build seconds and
+    queries/s at recall@10 >= 0.95 in the chosen precision form."""
+    import torch
+
+    B = W["build"]
+    prec = forms[chosen_form.split("+")[0]].precision
+    out = {}
+
+    def timer(fn, reps=2):
+        fn()
+        ev0.record(st)
+        for _ in range(reps):
+            fn()
+        ev1.record(st)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    parts = {}
+    for P in (4, 8):
+        part = datagen.even_partition(len(base), P, seed=17)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pidx = capi.nsg_build_partitioned(bt, part, B["K"], B["L"], B["R"], B["C"], seed=0)
+        torch.cuda.synchronize()
+        b_s = time.perf_counter() - t0
+        if prec:
+            pidx.prepare(prec)
+        prm = capi.SearchParams(0, 0, prec, 0, -1)
+        bufs = {}
+
+        def res(L):
+            k = kq(L)
+            if k not in bufs:
+                bufs[k] = pidx.search_partitioned(qt, k, L, params=prm)
+            return pidx.search_partitioned(qt, k, L, params=prm, out=bufs[k])
+
+        best, pts = sweep_point(W["L_grid"], lambda L: recall10(res(L)), lambda L: timer(lambda: res(L)), nq)
+        info = pidx.info()
+        parts[str(P)] = {"build_seconds": b_s, "build_ms_sum_of_subsets": {k: info[k] for k in (
+            "ms_knn", "ms_collect", "ms_prune", "ms_connect")}, "at_recall10_0.95": best, "sweep": pts}
+        del pidx
+    out["partitioned"] = {"form": chosen_form.split("+")[0], "partition": "even random (seed 17)", "P": parts}
+
+    nnd = capi.NnDescentParams(16, 16, 12, 0.001, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nidx = capi.nsg_build_ex(bt, B["K"], B["L"], B["R"], B["C"], seed=0, knn_params=nnd)
+    torch.cuda.synchronize()
+    b_s = time.perf_counter() - t0
+    ninfo = nidx.info()
+    # graph recall of the nn-descent kNN stage against the exact one, on sampled rows
+    rows = torch.arange(0, len(base), max(1, len(base) // 2000), device=bt.device)
+    ex_ids, _ = capi.nsg_knn_query(bt, bt[rows].contiguous(), B["K"] + 1)
+    nn_ids, _, _, _ = capi.nsg_knn_nndescent(bt, B["K"], nnd, with_d2=False)
+    ex_h, nn_h, rows_h = ex_ids.cpu().numpy(), nn_ids[rows].cpu().numpy(), rows.cpu().numpy()
+    g_rec = sum(len(set(nn_h[i]) & (set(ex_h[i]) - {int(rows_h[i])})) for i in range(len(rows_h))) / (
+        B["K"] * len(rows_h))
+    if prec:
+        nidx.prepare(prec)
+    prm = capi.SearchParams(0, 0, prec, 0, -1)
+    bufs = {}
+
+    def nres(L):
+        k = kq(L)
+        o = nidx.search_ex(qt, k, L, params=prm, out=bufs.get(k), counters=False)
+        bufs[k] = o
+        return o
+
+    best, pts = sweep_point(W["L_grid"], lambda L: recall10(nres(L)), lambda L: timer(lambda: nres(L)), nq)
+    out["nndescent"] = {"params": {"sample": 16, "reverse": 16, "iters": 12, "delta": 0.001},
+                        "iterations": ninfo["knn_iters"], "build_seconds": b_s,
+                        "build_ms": {k: ninfo[k] for k in ("ms_knn", "ms_collect", "ms_prune", "ms_connect",
+                                                            "ms_total")},
+                        "knn_graph_recall_vs_exact": g_rec, "graph_recall_rows": int(len(rows_h)),
+                        "form": chosen_form.split("+")[0], "at_recall10_0.95": best, "sweep": pts}
+    del nidx
+    return out
 
 
 def ground_truth(capi, bt, qt, W, k=10):
@@ -659,6 +762,9 @@ def main():
                "padded_k100_L500": {"value": job_qps(world, nq, ms_padded), "ms_per_step": ms_padded},
                "plan": pinfo}
 
+    extras = {} if args.no_extras else extra_legs(capi, datagen, bt, qt, gt, base, W, forms, chosen_form, nq, kq,
+                                                   recall10, ev0, ev1, st, args)
+
     peak, peak_kind = peaks()
     achieved = bytes_launch / (ms_step / 1e3) / 1e9
     src = kernel_source_hash()
@@ -726,6 +832,8 @@ def main():
                       "fp8_scale": info["fp8_scale"]},
             "per_query": {"n_expand": n_expand / nq, "n_dist": n_dist / nq},
             "batched": batched,
+            "partitioned": extras.get("partitioned"),
+            "nndescent": extras.get("nndescent"),
             "nsg_naive": naive,
             "learned_stop": {"train_queries": nq, "trace_L": list(STOP_TRACE_LS), "iters": STOP_ITERS,
                              "train_seconds": train_s, "loss_first": stop_loss[0].item(),

@@ -75,7 +75,17 @@ typedef struct {
     int32_t warps_per_query; /* 1 (default), 2 or 4 warps share each query: the same
                                 steps and results, more rows in flight per expansion
                                 (not with a stop model or a trace) */
+    int32_t pool;          /* where each query's pool of L keys lives: 0 auto (shared memory
+                              up to L = 1024, global memory above), 1 shared memory
+                              (L <= 1024), 2 global memory (L <= NSG_MAX_L: one L2-resident
+                              slot per resident warp, owned by the index -- or by the plan
+                              for nsg_plan_create -- and grown on demand; calls with global
+                              pools on one index on different streams at once race on it).
+                              The same steps and results either way. */
 } nsg_search_params;
+
+/* Largest pool size L of any search (global-memory pools; 1024 in shared memory). */
+#define NSG_MAX_L 8192
 
 /* Parameters of the early-termination MLP (8 features -> 64 ReLU -> 1):
  * w1[64][8], b1[64], w2[64], b2 in this order.  The features, formed before
@@ -108,6 +118,8 @@ typedef struct {
     int64_t prune_examined; /* candidates the MRNG edge selection examined over all nodes
                                (0 when not built here): per node, every candidate up to the
                                one that filled the row (R kept) or all of them */
+    int32_t parts;          /* subsets of a partitioned index (1: a single graph) */
+    int32_t knn_iters;      /* nn-descent iterations of the kNN stage (0: exact kNN) */
 } nsg_index_info_t;
 
 /* Human-readable name of a status code (static string). */
@@ -134,6 +146,46 @@ nsg_status nsg_knn_init(const float *base_dev, int64_t n, int32_t d, int32_t K,
                         int32_t *knn_ids_dev, float *knn_d2_dev, void *stream);
 nsg_status nsg_knn_query(const float *base_dev, int64_t n, int32_t d, const float *queries_dev,
                          int64_t nq, int32_t k, int32_t *ids_dev, float *d2_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Approximate kNN graph by nn-descent (Section 3.5 (ii): the build starts
+ *   from an approximate kNN graph; Section 3.6's indexing-complexity
+ *   paragraph: built with Dong, Charikar and Li's nn-descent for the
+ *   million-scale sets).  The published method, deterministic: node v starts
+ *   from the first K distinct ids != v among splitmix64(seed + v *
+ *   0x9e3779b97f4a7c15 + t) mod n (t = 0, 1, ...), all flagged new; each
+ *   iteration samples the first `sample` new and `sample` old entries of
+ *   every list (key order; the sampled new ones become old), keeps for every
+ *   node the `reverse` nearest of the nodes that sampled it (new and old
+ *   separately), joins NEW(v) = new samples u new reverse samples with itself
+ *   and with OLD(v) (old samples u old reverse samples, minus NEW(v)), and
+ *   cuts every list to the K smallest keys of itself and what it was offered
+ *   (entries not in it before are flagged new).  It stops after `iters`
+ *   iterations or once an iteration changes at most delta * n * K entries.
+ *   The result depends on the inputs alone; on integer data it equals the
+ *   CPU oracle's bit for bit.  Recall against the exact graph is the
+ *   caller's to measure.
+ * nsg_knn_nndescent: knn_ids_dev [n][K] i32 out, knn_d2_dev [n][K] f32 out
+ *   (nullable), sorted by key; iters_run / last_updates (host, nullable).
+ *   1 <= K < n, K <= 256.  Allocates scratch; synchronises once per
+ *   iteration.
+ * nsg_build_ex: nsg_build whose kNN stage (A1) is this nn-descent when
+ *   knn_params is non-NULL (the exact kNN otherwise).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t sample;  /* new (and old) entries sampled per list per iteration, 1..256 */
+    int32_t reverse; /* reverse samples kept per node (new and old each), 0..K */
+    int32_t iters;   /* iteration cap */
+    float delta;     /* stop once an iteration changes <= delta * n * K entries */
+    uint64_t seed;   /* initial random lists */
+} nsg_nndescent_params;
+
+nsg_status nsg_knn_nndescent(const float *base_dev, int64_t n, int32_t d, int32_t K,
+                             const nsg_nndescent_params *params, int32_t *knn_ids_dev, float *knn_d2_dev,
+                             int32_t *iters_run, int64_t *last_updates, void *stream);
+nsg_status nsg_build_ex(const float *base_dev, int64_t n, int32_t d, int32_t K, int32_t L, int32_t R,
+                        int32_t C, uint64_t seed, const nsg_nndescent_params *knn_params, void *stream,
+                        nsg_index **out);
 
 /* ---------------------------------------------------------------------------
  * A2. Centroid (Alg. 2, first step): c_j = (sum_i x_ij) / n, summed in FP64.
@@ -267,6 +319,38 @@ nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t
                          int32_t *status_dev, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Partition-and-merge (Section 4.2, the NSG-16core experiment: random
+ *   subsets, one NSG each, every query searched on every subset, results
+ *   merged; Section 4.3: the same split across machines).
+ * nsg_build_partitioned: part_host [n] i32 (HOST) gives each base row its
+ *   subset 0..P-1; every subset needs >= 2 rows.  Subset p's rows, in
+ *   ascending row order, get their own Alg. 2 build (kNN degree
+ *   min(K, |subset| - 1), the same L, R, C and seed), ids local to it.  The
+ *   index holds all subsets' graphs side by side in one allocation (subset p
+ *   at positions off_p .. off_{p+1}-1, its navigating node off_p + nav_p),
+ *   with the map from position to row id.  nsg_search / nsg_search_ex on it
+ *   search subset 0 only and return positions; nsg_save refuses it.  The
+ *   build phase times in nsg_index_info are sums over the subsets.
+ *   Synchronises the stream.
+ * nsg_search_partitioned: every query runs Alg. 1 on every subset's graph
+ *   with pool L (one launch over nq x P (query, subset) units), then one
+ *   warp per query merges the P result lists: the k smallest (distance, row
+ *   id) keys of their union, ids as ROW ids.  ids_dev [nq][k] i32 out,
+ *   d2_dev [nq][k] f32 out (nullable), -1 / +inf padded when the subsets
+ *   hold fewer than k rows in all.  params as nsg_search_ex, without the
+ *   learned stop or random initialisation (NSG_EINVAL).  Per-unit results
+ *   go to scratch owned by the index (grown on demand, so a larger batch
+ *   than any before allocates and synchronises once); calls on one index on
+ *   different streams at once race on it.  Asynchronous otherwise.
+ * ------------------------------------------------------------------------- */
+nsg_status nsg_build_partitioned(const float *base_dev, int64_t n, int32_t d, const int32_t *part_host,
+                                 int32_t P, int32_t K, int32_t L, int32_t R, int32_t C, uint64_t seed,
+                                 void *stream, nsg_index **out);
+nsg_status nsg_search_partitioned(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k,
+                                  int32_t L, const nsg_search_params *params, int32_t *ids_dev, float *d2_dev,
+                                  void *stream);
+
+/* ---------------------------------------------------------------------------
  * nsg_search_host: nsg_search_ex on HOST buffers (not in the paper: the
  *   serving-side call).  queries_host [nq][d] f32 in, ids_host [nq][k] i32
  *   out, d2_host [nq][k] f32 out (nullable); page-locked host memory copies
@@ -291,9 +375,11 @@ nsg_status nsg_search_host(const nsg_index *idx, const float *queries_host, int6
  * nsg_search_batched: one-shot form (derives the visiting order each call).
  * nsg_plan_create: binds an index, the query / k / L / output buffers and
  *   the parameters; derives the visiting order; with `autotune` times the
- *   candidate launch shapes (warps per query 1/2/4 x warps per block 2/4/8 x
- *   visited-hash slots 512/1024/2048; shapes with fewer warps per block than
- *   per query skipped, 24 in all) on the bound batch and keeps the fastest;
+ *   candidate launch shapes (pool placement shared / global memory -- global
+ *   only when Lmax > 1024, or fixed by params->pool -- x warps per query
+ *   1/2/4 x warps per block 2/4/8 x visited-hash slots 512/1024/2048; shapes
+ *   with fewer warps per block than per query skipped, 24 per placement) on
+ *   the bound batch and keeps the fastest;
  *   then captures
  *   "reset work counter + search" as a CUDA graph.  Synchronises.
  * nsg_plan_run: replays the graph on `stream` (asynchronous).
@@ -307,6 +393,7 @@ typedef struct {
     float best_ms;         /* time of one run of the chosen shape (autotune only) */
     float worst_ms;        /* slowest shape tried */
     int32_t warps_per_query; /* chosen warps per query */
+    int32_t pool;          /* chosen pool placement: 1 shared memory, 2 global memory */
 } nsg_plan_info_t;
 
 nsg_status nsg_search_batched(const nsg_index *idx, const float *queries_dev, int64_t nq, const int32_t *k_dev,

@@ -74,6 +74,8 @@ def _decl(L):
     L.orc_mrng_naive.argtypes = [P, i64, i32, P, P]
     L.orc_build_naive.argtypes = [P, i64, i32, i32, i32, i32, P, P]
     L.orc_search_random.argtypes = [P, P, i64, i32, P, i32, P, i64, i32, i32, i32, u64, i32, P, P, P, P]
+    L.orc_build_on_knn.argtypes = [P, i64, i32, P, i32, i32, i32, i32, u64, i32, P, P, P, P]
+    L.orc_nndescent.argtypes = [P, i64, i32, i32, i32, i32, i32, f32, u64, P, P, P, P]
     L.orc_recall_hits.argtypes = [P, i32, P, i32, i64, i32]
     L.orc_recall_hits.restype = i64
 
@@ -251,6 +253,22 @@ def build(base, K, L, R, Cap, seed=0, nthreads=None):
     return dict(adj=adj, deg=deg, nav=nav.value, n_added=added.value, knn=knn)
 
 
+def build_on_knn(base, knn, L, R, Cap, seed=0, nthreads=None):
+    """Alg. 2 after its kNN input, on a given kNN graph knn [n][K] (e.g. an
+    approximate one).  Returns dict(adj, deg, nav, n_added)."""
+    base = _f32(base)
+    knn = _i32(knn)
+    n, d = base.shape
+    adj = np.empty((n, R), np.int32)
+    deg = np.empty(n, np.int32)
+    nav = C.c_int32(0)
+    added = C.c_int32(0)
+    _check(lib().orc_build_on_knn(_p(base), n, d, _p(knn), knn.shape[1], L, R, Cap, seed,
+                                  nthreads or nthreads_default(), _p(adj), _p(deg), C.byref(nav), C.byref(added)),
+           "build_on_knn")
+    return dict(adj=adj, deg=deg, nav=nav.value, n_added=added.value)
+
+
 def build_naive(base, K, R, nthreads=None):
     """NSG-Naive (Section 4.1.2): MRNG edge selection over each node's K
     nearest neighbours; no navigating node, no connectivity pass.  Returns
@@ -317,6 +335,24 @@ def partition_search(base, queries, part, K, L_build, R, Cap, k, L, seed=0, nthr
         m = len(order)
         out_ids[q, :m], out_d2[q, :m] = gid[q, order], dist[q, order]
     return out_ids, out_d2
+
+
+def nndescent(base, K, S=16, Sr=16, iters=10, delta=0.001, seed=0):
+    """Approximate kNN graph by nn-descent (the approximate kNN graph the build
+    starts from, Sec. 3.5 (ii); Dong, Charikar and Li's method made
+    deterministic: seeded random init, per iteration S sampled new / old
+    entries and Sr reverse samples per node, local join, each list cut to its
+    K smallest keys).  Returns (ids [n][K], d2 [n][K], iterations run,
+    updates of the last iteration)."""
+    base = _f32(base)
+    n, d = base.shape
+    ids = np.empty((n, K), np.int32)
+    dist = np.empty((n, K), np.float32)
+    it = C.c_int32(0)
+    upd = C.c_int64(0)
+    _check(lib().orc_nndescent(_p(base), n, d, K, S, Sr, iters, delta, seed, _p(ids), _p(dist), C.byref(it),
+                               C.byref(upd)), "nndescent")
+    return ids, dist, it.value, upd.value
 
 
 def mrng_naive(base):

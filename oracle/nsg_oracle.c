@@ -761,6 +761,26 @@ int orc_select_all(const int32_t *knn, int32_t K, const float *base, int64_t n, 
  * search-collect-select per node -> connectivity.  knn_out ([n][K]) receives
  * the kNN graph when non-NULL.
  */
+/* Alg. 2 after its kNN input: centroid, navigating node, search-collect-
+ * select for every node, connectivity, on the given kNN graph knn [n][K]. */
+int orc_build_on_knn(const float *base, int64_t n, int32_t d, const int32_t *knn, int32_t K, int32_t l,
+                     int32_t R, int32_t C, uint64_t seed, int32_t nthreads, int32_t *adj, int32_t *deg,
+                     int32_t *nav_out, int32_t *n_added) {
+    if (!base || !knn || !adj || !deg || !nav_out || n < 2 || d < 1 || K < 1 || K >= n || l < 1 || R < 1 ||
+        C < R)
+        return ORC_EINVAL;
+    double *c = (double *)malloc(sizeof(double) * d);
+    int rc = orc_centroid(base, n, d, c);
+    int32_t r = (int32_t)(orc_splitmix64(seed) % (uint64_t)n);
+    int32_t nav = 0;
+    if (!rc) rc = orc_navigate(knn, n, K, base, d, c, r, l, &nav);
+    if (!rc) rc = orc_select_all(knn, K, base, n, d, nav, l, R, C, nthreads, adj, deg);
+    if (!rc) rc = orc_connect(adj, deg, n, R, base, d, nav, l, n_added, NULL, 0);
+    *nav_out = nav;
+    free(c);
+    return rc;
+}
+
 int orc_build(const float *base, int64_t n, int32_t d, int32_t K, int32_t l, int32_t R, int32_t C,
               uint64_t seed, int32_t nthreads, int32_t *adj, int32_t *deg, int32_t *nav_out,
               int32_t *n_added, int32_t *knn_out) {
@@ -768,17 +788,9 @@ int orc_build(const float *base, int64_t n, int32_t d, int32_t K, int32_t l, int
         R < 1 || C < R)
         return ORC_EINVAL;
     int32_t *knn = knn_out ? knn_out : (int32_t *)malloc(sizeof(int32_t) * (size_t)n * K);
-    double *c = (double *)malloc(sizeof(double) * d);
     int rc = orc_knn_rows(base, n, d, K, NULL, n, nthreads, knn, NULL);
-    if (!rc) rc = orc_centroid(base, n, d, c);
-    int32_t r = (int32_t)(orc_splitmix64(seed) % (uint64_t)n);
-    int32_t nav = 0;
-    if (!rc) rc = orc_navigate(knn, n, K, base, d, c, r, l, &nav);
-    if (!rc) rc = orc_select_all(knn, K, base, n, d, nav, l, R, C, nthreads, adj, deg);
-    if (!rc) rc = orc_connect(adj, deg, n, R, base, d, nav, l, n_added, NULL, 0);
-    *nav_out = nav;
+    if (!rc) rc = orc_build_on_knn(base, n, d, knn, K, l, R, C, seed, nthreads, adj, deg, nav_out, n_added);
     if (!knn_out) free(knn);
-    free(c);
     return rc;
 }
 
@@ -843,4 +855,221 @@ int64_t orc_recall_hits(const int32_t *ids, int32_t ld_ids, const int32_t *gt, i
                 }
         }
     return hits;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Approximate kNN graph by nn-descent (the approximate kNN graph the build  */
+/* starts from, Sec. 3.5 (ii) and the indexing-complexity paragraph of       */
+/* Sec. 3.6, built there with Dong, Charikar and Li's nn-descent).  The      */
+/* published method's steps, made deterministic (reading R13):               */
+/*   init: node v's list is the first K distinct ids != v among              */
+/*         splitmix64(seed + v * 0x9e3779b97f4a7c15 + t) mod n, t = 0, 1, ...*/
+/*         every entry flagged new;                                          */
+/*   each iteration, on the lists as they stand at its start:                */
+/*     1. newS(v) = the first S entries of v's list flagged new (key order), */
+/*        oldS(v) = the first S flagged old; newS entries become old;        */
+/*     2. reverse samples: rnew(u) = the Sr smallest keys (d(u,v), v) over   */
+/*        {v : u in newS(v)}, rold(u) likewise over oldS;                    */
+/*     3. NEW(v) = newS(v) u rnew(v), OLD(v) = (oldS(v) u rold(v)) \ NEW(v); */
+/*     4. local join: for every v, every p in NEW(v) and every q != p in     */
+/*        NEW(v) u OLD(v): q is offered to p and p to q, with key d(p, q);   */
+/*     5. each list becomes the K smallest keys of itself and its offers     */
+/*        (distinct ids); entries that were not in it are flagged new, and   */
+/*        their number is the iteration's update count;                      */
+/*   stop after `iters` iterations or once an iteration updates at most      */
+/*   delta * n * K entries.                                                  */
+/* The whole join of an iteration is computed first and the lists replaced  */
+/* afterwards, so no step depends on the order of the offers.               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double dist;
+    int32_t id;
+    int32_t isnew;
+} nd_entry;
+
+static int nd_cmp(const void *pa, const void *pb) {
+    const nd_entry *a = (const nd_entry *)pa, *b = (const nd_entry *)pb;
+    if (a->dist < b->dist) return -1;
+    if (a->dist > b->dist) return 1;
+    return (a->id > b->id) - (a->id < b->id);
+}
+
+/* offers to one node: a growable array */
+typedef struct {
+    nd_entry *e;
+    int64_t size, cap;
+} nd_vec;
+
+static int nd_push(nd_vec *v, double dist, int32_t id, int32_t isnew) {
+    if (v->size == v->cap) {
+        int64_t c = v->cap ? 2 * v->cap : 16;
+        nd_entry *p = (nd_entry *)realloc(v->e, sizeof(nd_entry) * (size_t)c);
+        if (!p) return ORC_ENOMEM;
+        v->e = p;
+        v->cap = c;
+    }
+    v->e[v->size].dist = dist;
+    v->e[v->size].id = id;
+    v->e[v->size].isnew = isnew;
+    v->size++;
+    return ORC_OK;
+}
+
+static int nd_has(const int32_t *ids, int32_t m, int32_t id) {
+    for (int32_t i = 0; i < m; ++i)
+        if (ids[i] == id) return 1;
+    return 0;
+}
+
+/* ids [n][K], dist [n][K] out (sorted by key); *iters_run and *last_updates
+ * (nullable) report the iterations run and the last iteration's updates. */
+int orc_nndescent(const float *base, int64_t n, int32_t d, int32_t K, int32_t S, int32_t Sr, int32_t iters,
+                  float delta, uint64_t seed, int32_t *ids, float *dist, int32_t *iters_run,
+                  int64_t *last_updates) {
+    if (!base || !ids || n < 2 || d < 1 || K < 1 || K >= n || S < 0 || Sr < 0 || iters < 0) return ORC_EINVAL;
+    nd_entry *list = (nd_entry *)malloc(sizeof(nd_entry) * (size_t)n * K);
+    int32_t *newS = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * (S > 0 ? S : 1));
+    int32_t *oldS = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * (S > 0 ? S : 1));
+    int32_t *nnew = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    int32_t *nold = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    nd_vec *rnew = (nd_vec *)calloc((size_t)n, sizeof(nd_vec));
+    nd_vec *rold = (nd_vec *)calloc((size_t)n, sizeof(nd_vec));
+    nd_vec *offers = (nd_vec *)calloc((size_t)n, sizeof(nd_vec));
+    int32_t cap = 2 * (S + Sr) + 2;
+    int32_t *NEWv = (int32_t *)malloc(sizeof(int32_t) * cap);
+    int32_t *OLDv = (int32_t *)malloc(sizeof(int32_t) * cap);
+    nd_entry *merged = (nd_entry *)malloc(sizeof(nd_entry) * (size_t)K);
+    int rc = ORC_OK;
+    if (!list || !newS || !oldS || !nnew || !nold || !rnew || !rold || !offers || !NEWv || !OLDv || !merged)
+        rc = ORC_ENOMEM;
+    /* init: K distinct random ids per node */
+    for (int64_t v = 0; !rc && v < n; ++v) {
+        nd_entry *L = list + v * K;
+        int32_t m = 0;
+        int32_t *got = (int32_t *)malloc(sizeof(int32_t) * K);
+        for (uint64_t t = 0; m < K; ++t) {
+            int32_t x = (int32_t)(orc_splitmix64(seed + (uint64_t)v * 0x9e3779b97f4a7c15ULL + t) % (uint64_t)n);
+            if (x == v || nd_has(got, m, x)) continue;
+            got[m] = x;
+            L[m].dist = (double)orc_dist2(base + v * d, base + (int64_t)x * d, d);
+            L[m].id = x;
+            L[m].isnew = 1;
+            m++;
+        }
+        free(got);
+        qsort(L, K, sizeof(nd_entry), nd_cmp);
+    }
+    int32_t it = 0;
+    int64_t updates = 0;
+    for (; !rc && it < iters; ++it) {
+        /* 1. samples */
+        for (int64_t v = 0; v < n; ++v) {
+            nd_entry *L = list + v * K;
+            nnew[v] = nold[v] = 0;
+            for (int32_t i = 0; i < K; ++i) {
+                if (L[i].isnew && nnew[v] < S) newS[v * S + nnew[v]++] = L[i].id;
+                else if (!L[i].isnew && nold[v] < S) oldS[v * S + nold[v]++] = L[i].id;
+            }
+            for (int32_t i = 0; i < K; ++i)
+                if (L[i].isnew && nd_has(newS + v * S, nnew[v], L[i].id)) L[i].isnew = 0;
+        }
+        /* 2. reverse samples (all, then the Sr smallest keys per node) */
+        for (int64_t v = 0; v < n; ++v) {
+            rnew[v].size = rold[v].size = 0;
+            offers[v].size = 0;
+        }
+        for (int64_t v = 0; !rc && v < n; ++v) {
+            const nd_entry *L = list + v * K;
+            for (int32_t i = 0; !rc && i < K; ++i) {
+                const int32_t u = L[i].id;
+                if (nd_has(newS + v * S, nnew[v], u)) rc = nd_push(&rnew[u], L[i].dist, (int32_t)v, 1);
+                else if (nd_has(oldS + v * S, nold[v], u)) rc = nd_push(&rold[u], L[i].dist, (int32_t)v, 0);
+            }
+        }
+        for (int64_t u = 0; !rc && u < n; ++u) {
+            qsort(rnew[u].e, rnew[u].size, sizeof(nd_entry), nd_cmp);
+            qsort(rold[u].e, rold[u].size, sizeof(nd_entry), nd_cmp);
+            if (rnew[u].size > Sr) rnew[u].size = Sr;
+            if (rold[u].size > Sr) rold[u].size = Sr;
+        }
+        /* 3 + 4. join sets and the local join, offers collected per node */
+        for (int64_t v = 0; !rc && v < n; ++v) {
+            int32_t a = 0, b = 0;
+            for (int32_t i = 0; i < nnew[v]; ++i)
+                if (!nd_has(NEWv, a, newS[v * S + i])) NEWv[a++] = newS[v * S + i];
+            for (int64_t i = 0; i < rnew[v].size; ++i)
+                if (!nd_has(NEWv, a, rnew[v].e[i].id)) NEWv[a++] = rnew[v].e[i].id;
+            for (int32_t i = 0; i < nold[v]; ++i)
+                if (!nd_has(NEWv, a, oldS[v * S + i]) && !nd_has(OLDv, b, oldS[v * S + i])) OLDv[b++] = oldS[v * S + i];
+            for (int64_t i = 0; i < rold[v].size; ++i)
+                if (!nd_has(NEWv, a, rold[v].e[i].id) && !nd_has(OLDv, b, rold[v].e[i].id)) OLDv[b++] = rold[v].e[i].id;
+            for (int32_t i = 0; !rc && i < a; ++i) {
+                const int32_t p = NEWv[i];
+                for (int32_t j = 0; !rc && j < a + b; ++j) {
+                    const int32_t q = j < a ? NEWv[j] : OLDv[j - a];
+                    if (q == p) continue;
+                    const double dd = (double)orc_dist2(base + (int64_t)p * d, base + (int64_t)q * d, d);
+                    rc = nd_push(&offers[p], dd, q, 1);
+                    if (!rc) rc = nd_push(&offers[q], dd, p, 1);
+                }
+            }
+        }
+        /* 5. each list: the K smallest of itself and its offers, distinct ids */
+        updates = 0;
+        for (int64_t p = 0; !rc && p < n; ++p) {
+            nd_entry *L = list + p * K;
+            nd_vec *o = &offers[p];
+            qsort(o->e, o->size, sizeof(nd_entry), nd_cmp);
+            int32_t m = 0, i = 0;
+            int64_t j = 0;
+            while (m < K && (i < K || j < o->size)) {
+                nd_entry e;
+                if (j >= o->size || (i < K && nd_cmp(&L[i], &o->e[j]) <= 0)) e = L[i++];
+                else e = o->e[j++];
+                /* an id offered again, or offered while in the list (same key: the
+                 * list's own entry, with its flag, comes first) is kept once */
+                int dup = 0;
+                for (int32_t t = 0; t < m; ++t)
+                    if (merged[t].id == e.id) dup = 1;
+                if (dup) continue;
+                merged[m++] = e;
+            }
+            for (int32_t t = 0; t < K; ++t) {
+                int was = 0;
+                for (int32_t r = 0; r < K; ++r)
+                    if (L[r].id == merged[t].id) was = 1;
+                if (!was) updates++;
+            }
+            memcpy(L, merged, sizeof(nd_entry) * (size_t)K);
+        }
+        if (!rc && updates <= (int64_t)((double)delta * (double)n * (double)K)) {
+            ++it;
+            break;
+        }
+    }
+    for (int64_t v = 0; !rc && v < n; ++v)
+        for (int32_t i = 0; i < K; ++i) {
+            ids[v * K + i] = list[v * K + i].id;
+            if (dist) dist[v * K + i] = (float)list[v * K + i].dist;
+        }
+    if (iters_run) *iters_run = it;
+    if (last_updates) *last_updates = updates;
+    for (int64_t v = 0; rnew && v < n; ++v) {
+        free(rnew[v].e);
+        free(rold[v].e);
+        free(offers[v].e);
+    }
+    free(list);
+    free(newS);
+    free(oldS);
+    free(nnew);
+    free(nold);
+    free(rnew);
+    free(rold);
+    free(offers);
+    free(NEWv);
+    free(OLDv);
+    free(merged);
+    return rc;
 }

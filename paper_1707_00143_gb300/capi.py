@@ -34,16 +34,30 @@ class SearchParams(C.Structure):
     _fields_ = [("max_steps", C.c_int32), ("hash_slots", C.c_int32), ("precision", C.c_int32),
                 ("warps_per_cta", C.c_int32), ("rerank", C.c_int32), ("stop_model", C.c_void_p),
                 ("stop_threshold", C.c_float), ("stop_k", C.c_int32), ("stop_min_steps", C.c_int32),
-                ("init_random", C.c_int32), ("init_seed", C.c_uint64), ("warps_per_query", C.c_int32)]
+                ("init_random", C.c_int32), ("init_seed", C.c_uint64), ("warps_per_query", C.c_int32),
+                ("pool", C.c_int32)]
 
     def __init__(self, max_steps=0, hash_slots=0, precision=0, warps_per_cta=0, rerank=-1, stop_model=None,
-                 stop_threshold=0.5, stop_k=0, stop_min_steps=0, init_random=0, init_seed=0, warps_per_query=1):
+                 stop_threshold=0.5, stop_k=0, stop_min_steps=0, init_random=0, init_seed=0, warps_per_query=1,
+                 pool=0):
         ptr = stop_model.data_ptr() if isinstance(stop_model, torch.Tensor) else stop_model
         super().__init__(max_steps, hash_slots, precision, warps_per_cta, rerank, ptr, stop_threshold, stop_k,
-                         stop_min_steps, init_random, init_seed, warps_per_query)
+                         stop_min_steps, init_random, init_seed, warps_per_query, pool)
 
 
 STOP_FEATURES, STOP_PARAMS = 8, 641
+POOL_AUTO, POOL_SHARED, POOL_GLOBAL = 0, 1, 2
+MAX_L = 8192
+
+
+class NnDescentParams(C.Structure):
+    """nn-descent settings: samples per list, reverse samples per node,
+    iteration cap, stopping fraction, seed of the initial lists."""
+    _fields_ = [("sample", C.c_int32), ("reverse", C.c_int32), ("iters", C.c_int32), ("delta", C.c_float),
+                ("seed", C.c_uint64)]
+
+    def __init__(self, sample=16, reverse=16, iters=10, delta=0.001, seed=0):
+        super().__init__(sample, reverse, iters, delta, seed)
 
 
 class IndexInfo(C.Structure):
@@ -53,7 +67,8 @@ class IndexInfo(C.Structure):
                 ("fp8_scale", C.c_float), ("ms_knn", C.c_float), ("ms_centroid_nav", C.c_float),
                 ("ms_collect", C.c_float), ("ms_prune", C.c_float), ("ms_connect", C.c_float),
                 ("ms_total", C.c_float), ("n_fixup_searches", C.c_int64), ("has_u8", C.c_int32),
-                ("u8_lo", C.c_float), ("u8_scale", C.c_float), ("prune_examined", C.c_int64)]
+                ("u8_lo", C.c_float), ("u8_scale", C.c_float), ("prune_examined", C.c_int64),
+                ("parts", C.c_int32), ("knn_iters", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -80,6 +95,10 @@ SIGNATURES = [
     ("nsg_search", [P, P, i64, i32, i32, P, P, P], i32),
     ("nsg_search_ex", [P, P, i64, i32, i32, P, P, P, P, P, P, P], i32),
     ("nsg_search_host", [P, P, i64, i32, i32, P, P, P, P], i32),
+    ("nsg_build_partitioned", [P, i64, i32, P, i32, i32, i32, i32, i32, u64, P, P], i32),
+    ("nsg_knn_nndescent", [P, i64, i32, i32, P, P, P, P, P, P], i32),
+    ("nsg_build_ex", [P, i64, i32, i32, i32, i32, i32, u64, P, P, P], i32),
+    ("nsg_search_partitioned", [P, P, i64, i32, i32, P, P, P, P], i32),
     ("nsg_recall", [P, i32, P, i32, i64, i32, P, P], i32),
     ("nsg_search_trace", [P, P, i64, i32, i32, P, P, P, P, P, i32, P], i32),
     ("nsg_search_batched", [P, P, i64, P, P, i32, i32, P, P, P, P, P], i32),
@@ -307,6 +326,20 @@ class Index:
                                      _stream()), "nsg_search_host")
         return dict(ids=ids, d2=d2)
 
+    def search_partitioned(self, queries, k, L, params=None, out=None):
+        """Partition-and-merge search on an index from nsg_build_partitioned:
+        every query on every subset, merged to the k smallest (d2, row id)."""
+        queries = _dev(queries, torch.float32)
+        nq = queries.shape[0]
+        dev = queries.device
+        if out is None:
+            out = dict(ids=torch.empty((nq, k), dtype=torch.int32, device=dev),
+                       d2=torch.empty((nq, k), dtype=torch.float32, device=dev))
+        p = params if params is not None else SearchParams()
+        _check(lib().nsg_search_partitioned(self.h, _ptr(queries), nq, k, L, C.byref(p), _ptr(out["ids"]),
+                                            _ptr(out["d2"]), _stream()), "nsg_search_partitioned")
+        return out
+
     def search_trace(self, queries, k, L, cap, params=None):
         """Fixed-L search recording per-step stop features and change flags."""
         queries = _dev(queries, torch.float32)
@@ -347,7 +380,8 @@ class Index:
 
 class PlanInfo(C.Structure):
     _fields_ = [("warps_per_cta", C.c_int32), ("hash_slots", C.c_int32), ("n_tried", C.c_int32),
-                ("best_ms", C.c_float), ("worst_ms", C.c_float), ("warps_per_query", C.c_int32)]
+                ("best_ms", C.c_float), ("worst_ms", C.c_float), ("warps_per_query", C.c_int32),
+                ("pool", C.c_int32)]
 
 
 class Plan:
@@ -388,6 +422,30 @@ class Plan:
             pass
 
 
+def nsg_knn_nndescent(base, K, params=None, with_d2=True):
+    """Approximate kNN graph by nn-descent.  Returns (ids, d2 or None,
+    iterations run, updates of the last iteration)."""
+    base = _dev(base, torch.float32)
+    n, d = base.shape
+    ids = torch.empty((n, K), dtype=torch.int32, device=base.device)
+    d2 = torch.empty((n, K), dtype=torch.float32, device=base.device) if with_d2 else None
+    p = params if params is not None else NnDescentParams()
+    it, upd = C.c_int32(0), C.c_int64(0)
+    _check(lib().nsg_knn_nndescent(_ptr(base), n, d, K, C.byref(p), _ptr(ids), _ptr(d2), C.byref(it),
+                                   C.byref(upd), _stream()), "nsg_knn_nndescent")
+    return ids, d2, it.value, upd.value
+
+
+def nsg_build_ex(base, K, L, R, Cap, seed=0, knn_params=None):
+    """nsg_build with the kNN stage by nn-descent when knn_params is given."""
+    base = _dev(base, torch.float32)
+    n, d = base.shape
+    h = C.c_void_p()
+    kp = C.byref(knn_params) if knn_params is not None else None
+    _check(lib().nsg_build_ex(_ptr(base), n, d, K, L, R, Cap, seed, kp, _stream(), C.byref(h)), "nsg_build_ex")
+    return Index(h)
+
+
 def nsg_build_naive(base, K, R, seed=0):
     """NSG-Naive: MRNG selection over the kNN graph's edges (no navigating
     node, no connectivity pass); search it with SearchParams(init_random=...)."""
@@ -403,6 +461,22 @@ def nsg_build(base, K, L, R, Cap, seed=0):
     n, d = base.shape
     h = C.c_void_p()
     _check(lib().nsg_build(_ptr(base), n, d, K, L, R, Cap, seed, _stream(), C.byref(h)), "nsg_build")
+    return Index(h)
+
+
+def nsg_build_partitioned(base, part, K, L, R, Cap, seed=0):
+    """Partition-and-merge index: one Alg. 2 build per subset (part: host
+    int32 [n] subset ids 0..P-1, P = max + 1)."""
+    import numpy as np
+
+    base = _dev(base, torch.float32)
+    n, d = base.shape
+    part = np.ascontiguousarray(np.asarray(part, dtype=np.int32))
+    if part.shape != (n,):
+        raise ValueError("part needs one subset id per base row")
+    h = C.c_void_p()
+    _check(lib().nsg_build_partitioned(_ptr(base), n, d, part.ctypes.data_as(C.c_void_p), int(part.max()) + 1,
+                                       K, L, R, Cap, seed, _stream(), C.byref(h)), "nsg_build_partitioned")
     return Index(h)
 
 

@@ -43,6 +43,7 @@ struct nsg_index {
     int64_t n_fixup = 0;
     int64_t n_fixup_searches = 0;  // fix-ups whose speculative search was stale and ran again
     int64_t prune_examined = 0;    // candidates the edge selection examined, all nodes
+    int knn_iters = 0;             // nn-descent iterations of the kNN stage (0: exact kNN)
     float ms[6] = {0, 0, 0, 0, 0, 0};
     // nsg_search_host: device staging for `host_cap` queries of up to
     // `host_k` results and a step-cap flag; one call at a time
@@ -53,6 +54,23 @@ struct nsg_index {
     mutable int *host_ids = nullptr;
     mutable float *host_d2 = nullptr;
     mutable int *host_flag = nullptr;
+    // partitioned index (Sections 4.2, 4.3): the subsets' graphs side by side,
+    // subset p at positions [part_off[p], part_off[p+1]); starts [parts] device
+    // (each subset's navigating node), perm [n] device (position -> row id)
+    int parts = 1;
+    int *starts = nullptr;
+    int *perm = nullptr;
+    std::vector<int64_t> part_off;
+    // nsg_search_partitioned: per-unit results before the merge, grown on demand
+    mutable std::mutex part_mu;
+    mutable int64_t part_cap = 0;
+    mutable int *part_ids = nullptr;
+    mutable float *part_d2 = nullptr;
+    // global-memory search pools (nsg_search_params.pool): one slot of L keys
+    // per resident warp, grown on demand
+    mutable std::mutex gpool_mu;
+    mutable uint64_t *gpool = nullptr;
+    mutable size_t gpool_bytes = 0;
 };
 
 namespace {
@@ -122,9 +140,8 @@ inline unsigned next_pow2(unsigned x) {
 // do not change), and 2 KB per warp keeps 28 warps resident per SM; measured
 // on the 1M x 128 workload, 512 slots beat 1024 and 2048 at L = 100..200.
 inline int default_hash(int L, int width) {
-    (void)L;
     (void)width;
-    return 512;
+    return L <= 1024 ? 512 : 2048;  // longer searches measure more nodes
 }
 inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -196,6 +213,37 @@ nsg_status knn_run(const float *bp, int64_t n, int dp, const float *qp, int64_t 
     int used = 0;
     if (!knn_force_scan()) NSG_CK(nsg::launch_knn_tc(l, &used, st));
     if (!used) NSG_CK(nsg::launch_knn_direct(l, st));
+    return NSG_OK;
+}
+
+bool nndescent_params_ok(const nsg_nndescent_params &p) {
+    return p.sample >= 1 && p.sample <= 256 && p.reverse >= 0 && p.reverse <= 256 && p.iters >= 0 &&
+           p.iters <= 1000 && p.delta >= 0.0f;
+}
+
+// Approximate kNN graph by nn-descent into ids [n][K] (d2 nullable), with
+// scratch allocated for the call.  base [n][dp] padded rows.
+nsg_status nndescent_run(const float *base, int64_t n, int dp, int K, const nsg_nndescent_params &p, int *ids,
+                         float *d2, int *iters_run, int64_t *last_updates, cudaStream_t st) {
+    DevBuf<unsigned char> scratch;
+    NSG_CK(scratch.alloc(nsg::nndescent_scratch_bytes(n, K, p.sample, p.reverse)));
+    nsg::NnDescentLaunch l;
+    l.base = base;
+    l.n = n;
+    l.dp = dp;
+    l.K = K;
+    l.S = p.sample;
+    l.Sr = p.reverse;
+    l.iters = p.iters;
+    l.delta = p.delta;
+    l.seed = p.seed;
+    l.ids = ids;
+    l.d2 = d2;
+    l.scratch = scratch.p;
+    l.iters_run = iters_run;
+    l.last_updates = last_updates;
+    NSG_CK(nsg::launch_nndescent(l, st));
+    NSG_CK(cudaStreamSynchronize(st));
     return NSG_OK;
 }
 
@@ -353,6 +401,11 @@ void destroy(nsg_index *ix) {
     if (ix->host_ids) cudaFree(ix->host_ids);
     if (ix->host_d2) cudaFree(ix->host_d2);
     if (ix->host_flag) cudaFree(ix->host_flag);
+    if (ix->starts) cudaFree(ix->starts);
+    if (ix->perm) cudaFree(ix->perm);
+    if (ix->part_ids) cudaFree(ix->part_ids);
+    if (ix->part_d2) cudaFree(ix->part_d2);
+    if (ix->gpool) cudaFree(ix->gpool);
     delete ix;
 }
 
@@ -596,8 +649,8 @@ nsg_status nsg_build_naive(const float *base_dev, int64_t n, int32_t d, int32_t 
     return NSG_OK;
 }
 
-nsg_status nsg_build(const float *base_dev, int64_t n, int32_t d, int32_t K, int32_t L, int32_t R,
-                     int32_t C, uint64_t seed, void *stream, nsg_index **out) {
+static nsg_status build_index(const float *base_dev, int64_t n, int32_t d, int32_t K, int32_t L, int32_t R,
+                       int32_t C, uint64_t seed, const nsg_nndescent_params *nnd, void *stream, nsg_index **out) {
     if (!out) return NSG_EINVAL;
     *out = nullptr;
     if (!base_dev || n < 2 || n >= INT32_MAX || d < 1 || d > 4 * nsg::MAX_DP4_HOST || K < 1 || K >= n ||
@@ -619,9 +672,10 @@ nsg_status nsg_build(const float *base_dev, int64_t n, int32_t d, int32_t K, int
     if (!s && (e = adj.alloc((size_t)n * R)) != cudaSuccess) s = cuda_fail(e, "alloc adj");
     if (!s && (e = deg.alloc((size_t)n)) != cudaSuccess) s = cuda_fail(e, "alloc deg");
     if (!s && (e = knn.alloc((size_t)n * K)) != cudaSuccess) s = cuda_fail(e, "alloc knn");
-    // A1: kNN graph
+    // A1: kNN graph, exact or by nn-descent
     auto t0 = std::chrono::steady_clock::now();
-    if (!s) s = knn_run(base.p, n, ix->dp, base.p, n, 0, K, 1, knn.p, nullptr, st);
+    if (!s && !nnd) s = knn_run(base.p, n, ix->dp, base.p, n, 0, K, 1, knn.p, nullptr, st);
+    if (!s && nnd) s = nndescent_run(base.p, n, ix->dp, K, *nnd, knn.p, nullptr, &ix->knn_iters, nullptr, st);
     if (!s && (e = cudaStreamSynchronize(st)) != cudaSuccess) s = cuda_fail(e, "knn");
     ix->ms[0] = (float)since_ms(t0);
     // A2 + A3: centroid and navigating node
@@ -661,6 +715,44 @@ nsg_status nsg_build(const float *base_dev, int64_t n, int32_t d, int32_t K, int
     }
     *out = ix;
     return NSG_OK;
+}
+
+nsg_status nsg_build(const float *base_dev, int64_t n, int32_t d, int32_t K, int32_t L, int32_t R,
+                     int32_t C, uint64_t seed, void *stream, nsg_index **out) {
+    return build_index(base_dev, n, d, K, L, R, C, seed, nullptr, stream, out);
+}
+
+nsg_status nsg_build_ex(const float *base_dev, int64_t n, int32_t d, int32_t K, int32_t L, int32_t R,
+                        int32_t C, uint64_t seed, const nsg_nndescent_params *knn_params, void *stream,
+                        nsg_index **out) {
+    if (knn_params && (!nndescent_params_ok(*knn_params) || knn_params->reverse > K)) {
+        if (out) *out = nullptr;
+        return NSG_EINVAL;
+    }
+    return build_index(base_dev, n, d, K, L, R, C, seed, knn_params, stream, out);
+}
+
+nsg_status nsg_knn_nndescent(const float *base_dev, int64_t n, int32_t d, int32_t K,
+                             const nsg_nndescent_params *params, int32_t *knn_ids_dev, float *knn_d2_dev,
+                             int32_t *iters_run, int64_t *last_updates, void *stream) {
+    return host_guard([&]() -> nsg_status {
+        if (!base_dev || !knn_ids_dev || !params || n < 2 || n >= INT32_MAX || d < 1 ||
+            d > 4 * nsg::MAX_DP4_HOST || K < 1 || K >= n || K > 256 || !nndescent_params_ok(*params) ||
+            params->reverse > K)
+            return NSG_EINVAL;
+        cudaStream_t st = S(stream);
+        DevBuf<float> tmp;
+        const float *view = nullptr;
+        nsg_status s = padded_view(base_dev, n, d, tmp, &view, st);
+        if (s) return s;
+        int it = 0;
+        int64_t upd = 0;
+        s = nndescent_run(view, n, round_up4(d), K, *params, knn_ids_dev, knn_d2_dev, &it, &upd, st);
+        if (s) return s;
+        if (iters_run) *iters_run = it;
+        if (last_updates) *last_updates = upd;
+        return NSG_OK;
+    });
 }
 
 nsg_status nsg_index_from_graph(const float *base_dev, int64_t n, int32_t d, const int32_t *adj_dev,
@@ -728,16 +820,105 @@ nsg_status nsg_index_from_graph(const float *base_dev, int64_t n, int32_t d, con
     });
 }
 
+nsg_status nsg_build_partitioned(const float *base_dev, int64_t n, int32_t d, const int32_t *part_host,
+                                 int32_t P, int32_t K, int32_t L, int32_t R, int32_t C, uint64_t seed,
+                                 void *stream, nsg_index **out) {
+    return host_guard([&]() -> nsg_status {
+        if (!out) return NSG_EINVAL;
+        *out = nullptr;
+        if (!base_dev || !part_host || n < 2 || n >= INT32_MAX || d < 1 || d > 4 * nsg::MAX_DP4_HOST || P < 1 ||
+            P > 4096 || K < 1 || L < 1 || L > 1024 || R < 1 || R > 1024 || C < R || C > 4096)
+            return NSG_EINVAL;
+        // subsets in ascending id, rows of a subset in ascending row order
+        std::vector<int64_t> off((size_t)P + 1, 0);
+        for (int64_t i = 0; i < n; ++i) {
+            const int p = part_host[i];
+            if (p < 0 || p >= P) return NSG_EINVAL;
+            ++off[(size_t)p + 1];
+        }
+        for (int p = 0; p < P; ++p) {
+            if (off[(size_t)p + 1] < 2) return NSG_EINVAL;  // every subset needs 2 rows
+            off[(size_t)p + 1] += off[(size_t)p];
+        }
+        std::vector<int> perm((size_t)n);
+        {
+            std::vector<int64_t> fill(off.begin(), off.end() - 1);
+            for (int64_t i = 0; i < n; ++i) perm[(size_t)fill[(size_t)part_host[i]]++] = (int)i;
+        }
+        cudaStream_t st = S(stream);
+        auto t_all = std::chrono::steady_clock::now();
+        DevBuf<int> perm_d, adj, deg, starts_d;
+        DevBuf<float> rows;  // the base in subset order, [n][d]
+        NSG_CK(perm_d.alloc((size_t)n));
+        NSG_CK(adj.alloc((size_t)n * R));
+        NSG_CK(deg.alloc((size_t)n));
+        NSG_CK(starts_d.alloc((size_t)P));
+        NSG_CK(rows.alloc((size_t)n * d));
+        NSG_CK(cudaMemcpyAsync(perm_d.p, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+        NSG_CK(nsg::launch_gather_rows(base_dev, n, d, perm_d.p, rows.p, st));
+        std::vector<int> starts((size_t)P);
+        float ms[5] = {0, 0, 0, 0, 0};
+        int64_t fixups = 0, researched = 0, examined = 0;
+        for (int p = 0; p < P; ++p) {
+            const int64_t o = off[(size_t)p], np = off[(size_t)p + 1] - o;
+            const int Kp = (int)std::min<int64_t>(K, np - 1);
+            nsg_index *sub = nullptr;
+            nsg_status s = nsg_build(rows.p + o * d, np, d, Kp, L, R, C, seed, stream, &sub);
+            if (s) return s;
+            std::unique_ptr<nsg_index, void (*)(nsg_index *)> hold(sub, destroy);
+            NSG_CK(nsg::launch_offset_adj(sub->adj, np, R, (int)o, adj.p + o * R, st));
+            NSG_CK(cudaMemcpyAsync(deg.p + o, sub->deg, sizeof(int) * np, cudaMemcpyDeviceToDevice, st));
+            NSG_CK(cudaStreamSynchronize(st));
+            starts[(size_t)p] = (int)o + sub->nav;
+            for (int t = 0; t < 5; ++t) ms[t] += sub->ms[t];
+            fixups += sub->n_fixup;
+            researched += sub->n_fixup_searches;
+            examined += sub->prune_examined;
+        }
+        NSG_CK(cudaMemcpyAsync(starts_d.p, starts.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
+        nsg_index *ix = new (std::nothrow) nsg_index;
+        if (!ix) return NSG_ENOMEM;
+        std::unique_ptr<nsg_index, void (*)(nsg_index *)> hold(ix, destroy);
+        ix->n = n;
+        ix->d = d;
+        ix->dp = round_up4(d);
+        ix->R = R;
+        ix->nav = starts[0];
+        DevBuf<float> base;
+        nsg_status s = padded_copy(rows.p, n, d, ix->dp, base, st);
+        if (s) return s;
+        NSG_CK(cudaStreamSynchronize(st));
+        ix->base = base.release();
+        ix->adj = adj.release();
+        ix->deg = deg.release();
+        ix->parts = P;
+        ix->starts = starts_d.release();
+        ix->perm = perm_d.release();
+        ix->part_off = off;
+        for (int t = 0; t < 5; ++t) ix->ms[t] = ms[t];
+        ix->n_fixup = fixups;
+        ix->n_fixup_searches = researched;
+        ix->prune_examined = examined;
+        s = finish_index(ix, st);
+        if (s) return s;
+        ix->ms[5] = (float)since_ms(t_all);
+        *out = hold.release();
+        return NSG_OK;
+    });
+}
+
 namespace {
 
 // Validated launch description for nsg_search_ex / nsg_search_trace.
 nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k, int32_t L,
                        const nsg_search_params *params, int32_t *ids_dev, float *d2_dev, int32_t *n_expand_dev,
                        int32_t *n_dist_dev, int32_t *status_dev, nsg::SearchLaunch &l) {
-    if (!idx || k < 1 || L < k || L > 1024 || nq < 0 || nq >= INT32_MAX) return NSG_EINVAL;
+    if (!idx || k < 1 || L < k || L > NSG_MAX_L || nq < 0 || nq >= INT32_MAX) return NSG_EINVAL;
     if (nq > 0 && (!queries_dev || !ids_dev)) return NSG_EINVAL;
-    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0, 0, 0, 1};
+    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0, 0, 0, 1, 0};
     if (params) p = *params;
+    if (p.pool < 0 || p.pool > 2 || (p.pool == 1 && L > 1024)) return NSG_EINVAL;
+    l.pool_global = p.pool == 2 || (p.pool == 0 && L > 1024);
     if (p.precision < NSG_PREC_F32 || p.precision > NSG_PREC_U8) return NSG_EINVAL;
     if (p.init_random < 0 || p.init_random > L) return NSG_EINVAL;
     if (p.warps_per_query != 0 && p.warps_per_query != 1 && p.warps_per_query != 2 && p.warps_per_query != 4)
@@ -796,7 +977,32 @@ nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t n
 // counter is one of the index's kWorkSlots, taken round-robin and zeroed on
 // the launch's stream, so calls on one stream are ordered and up to
 // kWorkSlots calls may run concurrently on different streams.
+// Global-memory pools for a launch that asks for them: the index's slots,
+// grown (after the stream has drained) when this L needs more bytes.
+nsg_status ensure_gpool_body(const nsg_index *idx, nsg::SearchLaunch &l, cudaStream_t st) {
+    if (!l.pool_global) return NSG_OK;
+    const int64_t slots = nsg::search_pool_slots();
+    const size_t need = (size_t)slots * (size_t)l.L * sizeof(uint64_t);
+    std::lock_guard<std::mutex> lock(idx->gpool_mu);
+    if (need > idx->gpool_bytes) {
+        NSG_CK(cudaStreamSynchronize(st));
+        if (idx->gpool) cudaFree(idx->gpool);
+        idx->gpool = nullptr;
+        idx->gpool_bytes = 0;
+        NSG_CK(cudaMalloc(reinterpret_cast<void **>(&idx->gpool), need));
+        idx->gpool_bytes = need;
+    }
+    l.gpool = idx->gpool;
+    l.gpool_slots = slots;
+    return NSG_OK;
+}
+
+nsg_status ensure_gpool(const nsg_index *idx, nsg::SearchLaunch &l, cudaStream_t st) {
+    return host_guard([&] { return ensure_gpool_body(idx, l, st); });
+}
+
 nsg_status launch_dynamic(const nsg_index *idx, nsg::SearchLaunch l, cudaStream_t st) {
+    if (nsg_status s = ensure_gpool(idx, l, st)) return s;
     int *ctr = idx->work + (idx->work_next.fetch_add(1, std::memory_order_relaxed) % kWorkSlots);
     NSG_CK(cudaMemsetAsync(ctr, 0, sizeof(int), st));
     l.work = ctr;
@@ -814,6 +1020,45 @@ nsg_status nsg_search_ex(const nsg_index *idx, const float *queries_dev, int64_t
                                status_dev, l);
     if (s || nq == 0) return s;
     return launch_dynamic(idx, l, S(stream));
+}
+
+nsg_status nsg_search_partitioned(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k,
+                                  int32_t L, const nsg_search_params *params, int32_t *ids_dev, float *d2_dev,
+                                  void *stream) {
+    return host_guard([&]() -> nsg_status {
+        if (!idx || idx->parts < 2 || !idx->starts || !idx->perm || (nq > 0 && !ids_dev)) return NSG_EINVAL;
+        if (params && (params->stop_model || params->init_random)) return NSG_EINVAL;
+        const int P = idx->parts;
+        if (nq < 0 || nq >= INT32_MAX / P) return NSG_EINVAL;
+        nsg::SearchLaunch l;
+        // units (query, subset); their result rows [nq * P][k] go to scratch
+        int32_t *iph = reinterpret_cast<int32_t *>(16);
+        nsg_status s = make_search(idx, queries_dev, nq * P, k, L, params, iph, nullptr, nullptr, nullptr,
+                                   nullptr, l);
+        if (s || nq == 0) return s;
+        cudaStream_t st = S(stream);
+        std::lock_guard<std::mutex> lock(idx->part_mu);
+        const int64_t need = nq * P * (int64_t)k;
+        if (need > idx->part_cap) {
+            NSG_CK(cudaStreamSynchronize(st));
+            if (idx->part_ids) cudaFree(idx->part_ids);
+            if (idx->part_d2) cudaFree(idx->part_d2);
+            idx->part_ids = nullptr;
+            idx->part_d2 = nullptr;
+            idx->part_cap = 0;
+            NSG_CK(cudaMalloc(reinterpret_cast<void **>(&idx->part_ids), sizeof(int) * need));
+            NSG_CK(cudaMalloc(reinterpret_cast<void **>(&idx->part_d2), sizeof(float) * need));
+            idx->part_cap = need;
+        }
+        l.ids = idx->part_ids;
+        l.d2 = idx->part_d2;
+        l.parts = P;
+        l.starts = idx->starts;
+        s = launch_dynamic(idx, l, st);
+        if (s) return s;
+        NSG_CK(nsg::launch_merge_parts(idx->part_ids, idx->part_d2, nq, P, k, idx->perm, k, ids_dev, d2_dev, st));
+        return NSG_OK;
+    });
 }
 
 nsg_status nsg_search_host(const nsg_index *idx, const float *queries_host, int64_t nq, int32_t k, int32_t L,
@@ -882,9 +1127,10 @@ struct nsg_plan {
     nsg::SearchLaunch l;
     int *order = nullptr;  // visiting order (longest pool first)
     int *work = nullptr;   // device work counter
+    uint64_t *gpool = nullptr;  // global-memory pool slots (the graph keeps the address)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    nsg_plan_info_t info = {0, 0, 0, 0.0f, 0.0f};
+    nsg_plan_info_t info = {0, 0, 0, 0.0f, 0.0f, 1, 1};
 };
 
 namespace {
@@ -893,6 +1139,7 @@ void plan_destroy(nsg_plan *p) {
     if (!p) return;
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->gpool) cudaFree(p->gpool);
     if (p->order) cudaFree(p->order);
     if (p->work) cudaFree(p->work);
     delete p;
@@ -954,6 +1201,7 @@ nsg_status nsg_search_batched(const nsg_index *idx, const float *queries_dev, in
     nsg_status s = batched_setup(idx, queries_dev, nq, k_dev, L_dev, kmax, Lmax, params, ids_dev, d2_dev,
                                  status_dev, l, order, work, st);
     if (s) return s;
+    if ((s = ensure_gpool(idx, l, st))) return s;
     s = batched_run(l, st);
     if (s) return s;
     NSG_CK(cudaStreamSynchronize(st));  // the order / counter scratch is freed on return
@@ -979,13 +1227,33 @@ nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64
     }
     p->order = order.release();
     p->work = work.release();
+    // the plan's own global-memory pool slots (its graph keeps their address):
+    // needed above L = 1024, and tried by the autotuner below that
+    const bool want_gpool = p->l.pool_global || (autotune && (!params || params->pool == 0));
+    if (want_gpool) {
+        const int64_t slots = nsg::search_pool_slots();
+        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p->gpool), (size_t)slots * Lmax * sizeof(uint64_t));
+        if (e != cudaSuccess) {
+            plan_destroy(p);
+            return cuda_fail(e, "plan pool");
+        }
+        p->l.gpool_slots = slots;
+        if (p->l.pool_global) p->l.gpool = p->gpool;
+    }
     if (autotune) {  // time each launch shape on the bound batch; keep the fastest
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best = 1e30f, worst = 0.0f;
         int bw = 0, bh = 0, bq = 1, tried = 0;
+        uint64_t *bp = p->l.gpool;
         const bool groups_ok = p->l.stop_model == nullptr;  // the stop kernels run one warp per query
+        // pool placement: shared memory where L fits (<= 1024) unless the caller
+        // fixed it, global memory when the plan holds slots
+        std::vector<uint64_t *> pools;
+        if (!p->l.pool_global) pools.push_back(nullptr);
+        if (p->gpool) pools.push_back(p->gpool);
+        for (uint64_t *gp : pools)
         for (int q : {1, 2, 4})
             for (int w : {2, 4, 8})
             for (int h : {512, 1024, 2048}) {
@@ -994,6 +1262,7 @@ nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64
                 t.warps_per_cta = w;
                 t.hash_slots = h;
                 t.warps_per_query = q;
+                t.gpool = gp;
                 if (batched_run(t, st) || cudaStreamSynchronize(st) != cudaSuccess) continue;
                 cudaEventRecord(e0, st);
                 bool ok = true;
@@ -1010,6 +1279,7 @@ nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64
                     bw = w;
                     bh = h;
                     bq = q;
+                    bp = gp;
                 }
             }
         cudaEventDestroy(e0);
@@ -1018,6 +1288,7 @@ nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64
             p->l.warps_per_cta = bw;
             p->l.hash_slots = bh;
             p->l.warps_per_query = bq;
+            p->l.gpool = bp;
             p->info.best_ms = best;
             p->info.worst_ms = worst;
         }
@@ -1026,6 +1297,7 @@ nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64
     p->info.warps_per_cta = p->l.warps_per_cta > 0 ? p->l.warps_per_cta : 4;
     p->info.hash_slots = p->l.hash_slots;
     p->info.warps_per_query = p->l.warps_per_query;
+    p->info.pool = p->l.gpool ? 2 : 1;
     // capture "reset counter + search" once; a run replays it
     s = batched_run(p->l, st);  // sets kernel attributes outside the capture
     cudaError_t e = cudaStreamSynchronize(st);
@@ -1068,7 +1340,7 @@ nsg_status nsg_search_trace(const nsg_index *idx, const float *queries_dev, int6
                             const nsg_search_params *params, int32_t *ids_dev, float *feat_dev,
                             uint8_t *flag_dev, int32_t *steps_dev, int32_t cap, void *stream) {
     if (cap < 1 || (nq > 0 && (!feat_dev || !flag_dev || !steps_dev))) return NSG_EINVAL;
-    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0, 0, 0, 1};
+    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0, 0, 0, 1, 0};
     if (params) p = *params;
     p.stop_model = nullptr;  // traces record the fixed-L search
     nsg::SearchLaunch l;
@@ -1077,6 +1349,7 @@ nsg_status nsg_search_trace(const nsg_index *idx, const float *queries_dev, int6
     l.trace_feat = feat_dev;
     l.trace_flag = flag_dev;
     l.trace_cap = cap;
+    if ((s = ensure_gpool(idx, l, S(stream)))) return s;
     NSG_CK(nsg::launch_search(l, S(stream)));
     return NSG_OK;
 }
@@ -1144,7 +1417,7 @@ nsg_status nsg_index_prepare(nsg_index *idx, int32_t precision, void *stream) {
 
 nsg_status nsg_search(const nsg_index *idx, const float *queries_dev, int64_t nq, int32_t k, int32_t L,
                       int32_t *ids_dev, float *d2_dev, void *stream) {
-    if (!idx || k < 1 || L < k || L > 1024 || nq < 0 || nq >= INT32_MAX) return NSG_EINVAL;
+    if (!idx || k < 1 || L < k || L > NSG_MAX_L || nq < 0 || nq >= INT32_MAX) return NSG_EINVAL;
     if (nq == 0) return NSG_OK;
     if (!queries_dev || !ids_dev) return NSG_EINVAL;
     cudaStream_t st = S(stream);
@@ -1169,6 +1442,7 @@ nsg_status nsg_search(const nsg_index *idx, const float *queries_dev, int64_t nq
     l.n_dist = nullptr;
     l.status = nullptr;
     l.any_capped = idx->flag;
+    l.pool_global = L > 1024;
     NSG_CK(cudaMemsetAsync(idx->flag, 0, sizeof(int), st));
     if (nsg_status ls = launch_dynamic(idx, l, st)) return ls;
     int h = 0;
@@ -1213,6 +1487,9 @@ nsg_status nsg_index_info(const nsg_index *idx, nsg_index_info_t *info) {
     info->ms_prune = idx->ms[3];
     info->ms_connect = idx->ms[4];
     info->ms_total = idx->ms[5];
+    info->parts = idx->parts;
+    info->knn_iters = idx->knn_iters;
+    if (idx->parts > 1) info->device_bytes += (int64_t)idx->n * 4 + idx->parts * 4;
     return NSG_OK;
 }
 
@@ -1229,7 +1506,7 @@ static const char kMagic[8] = {'N', 'S', 'G', 'G', 'B', '3', '0', '0'};
 
 nsg_status nsg_save(const nsg_index *idx, const char *path) {
     return host_guard([&]() -> nsg_status {
-        if (!idx || !path) return NSG_EINVAL;
+        if (!idx || !path || idx->parts > 1) return NSG_EINVAL;
         const int64_t n = idx->n;
         std::vector<int> deg((size_t)n), adj((size_t)n * idx->R);
         std::vector<float> base((size_t)n * idx->d);

@@ -207,6 +207,31 @@ __device__ __forceinline__ bool visit(uint32_t *h, uint32_t mask, int shift, int
 #endif
 }
 
+// Removes id from the visited set if it is there (the set forgets it: a later
+// visit reports it new, so its distance is measured again).  Not concurrent
+// with visit() by other lanes on the same id.
+__device__ __forceinline__ void unvisit(uint32_t *h, uint32_t mask, int shift, int id) {
+    const uint32_t u = (uint32_t)id;
+#if NSG_HASH_WAYS == 4
+    const uint32_t bmask = mask >> 2;
+    uint32_t b = (u * 2654435761u) >> (shift + 2);
+#pragma unroll 1
+    for (int t = 0; t < HASH_BUCKET_PROBES; ++t) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (h[b * 4 + j] == u) h[b * 4 + j] = HASH_EMPTY;
+        b = (b + 1) & bmask;
+    }
+#else
+    uint32_t s = (u * 2654435761u) >> shift;
+#pragma unroll 1
+    for (int t = 0; t < HASH_PROBES; ++t) {
+        if (h[s] == u) h[s] = HASH_EMPTY;
+        s = (s + 1) & mask;
+    }
+#endif
+}
+
 __device__ __forceinline__ void hash_clear(uint32_t *h, int slots) {
     uint4 *h4 = reinterpret_cast<uint4 *>(h);
     const uint4 e = make_uint4(HASH_EMPTY, HASH_EMPTY, HASH_EMPTY, HASH_EMPTY);

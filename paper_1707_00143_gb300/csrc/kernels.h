@@ -54,8 +54,53 @@ struct SearchLaunch {
     // random initial pool of init_count seeded draws (0: start at `start`)
     int init_count = 0;
     uint64_t init_seed = 0;
+    // partitioned search: nq counts (query, subset) units, unit t searches
+    // query t / parts from starts[t % parts] and writes output row t
+    int parts = 1;
+    const int *starts = nullptr;
+    // pool placement: shared memory (gpool == nullptr, L <= 1024) or one slot
+    // of L keys per resident warp (group) in global memory, gpool_slots slots
+    int pool_global = 0;
+    uint64_t *gpool = nullptr;
+    int64_t gpool_slots = 0;
 };
+// Approximate kNN graph by nn-descent (nndescent.cu).  base [n][dp] padded
+// rows; ids [n][K] out, d2 [n][K] out (nullable); scratch: at least
+// nndescent_scratch_bytes(n, K, S, Sr) bytes, 16-byte aligned.  Synchronises
+// the stream once per iteration (the stopping rule reads the update count).
+struct NnDescentLaunch {
+    const float *base;
+    int64_t n;
+    int dp;
+    int K, S, Sr, iters;
+    float delta;
+    uint64_t seed;
+    int *ids;
+    float *d2;
+    void *scratch;
+    int *iters_run;         // host, nullable
+    int64_t *last_updates;  // host, nullable
+};
+size_t nndescent_scratch_bytes(int64_t n, int K, int S, int Sr);
+cudaError_t launch_nndescent(const NnDescentLaunch &l, cudaStream_t st);
+
+// Resident warps (groups) of any search launch on this device: an upper bound
+// on the global-memory pool slots a launch uses (the search kernels hold at
+// most 32 warps per SM).
+int64_t search_pool_slots();
 cudaError_t launch_search(const SearchLaunch &a, cudaStream_t st);
+
+// Partition-and-merge: per query, the union of `parts` sorted result lists
+// (ids_in [nq][parts][k_in], positions in the partitioned index, -1 padded;
+// d2_in likewise) mapped to row ids through perm and cut to the k smallest
+// (distance, row id) keys: ids_out [nq][k], d2_out [nq][k], -1 / +inf padded.
+cudaError_t launch_merge_parts(const int *ids_in, const float *d2_in, int64_t nq, int parts, int k_in,
+                               const int *perm, int k, int *ids_out, float *d2_out, cudaStream_t st);
+// rows of base [n][d] in the order of perm: out[i] = base[perm[i]]
+cudaError_t launch_gather_rows(const float *base, int64_t n, int d, const int *perm, float *out, cudaStream_t st);
+// adjacency rows of one subset, shifted to its place in the partitioned
+// index: out[v][j] = in[v][j] + offset (or -1) for v < nv
+cudaError_t launch_offset_adj(const int *in, int64_t nv, int R, int offset, int *out, cudaStream_t st);
 
 // Training of the early-termination MLP on search traces (full-batch Adam).
 // feat [nq][cap][8], flag [nq][cap], steps [nq]; label of step t of query q =

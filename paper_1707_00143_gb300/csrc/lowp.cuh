@@ -99,6 +99,10 @@ struct DistU8 {
         __syncwarp();
     }
     __device__ __forceinline__ void prefetch(const int *, int) const {}  // measured: no gain
+    // every row, ahead of a gather that comes later
+    __device__ __forceinline__ void prefetch_all(const int *ids, int m) const {
+        prefetch_rows_l2(base, dc * 16, ids, m);
+    }
 };
 
 template <int P>
@@ -202,6 +206,10 @@ struct DistLp {
         __syncwarp();
     }
     __device__ __forceinline__ void prefetch(const int *, int) const {}  // measured: no gain
+    // every row, ahead of a gather that comes later
+    __device__ __forceinline__ void prefetch_all(const int *ids, int m) const {
+        prefetch_rows_l2(base, dc * 16, ids, m);
+    }
 };
 
 }  // namespace nsg

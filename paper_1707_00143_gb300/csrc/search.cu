@@ -1,311 +1,8 @@
 // search.cu -- Alg. 1 for a batch of queries (search on NSG, Section 3.6) and
 // the per-node search-and-collect of Alg. 2 (Section 3.5 iii), one warp per unit.
-#include <algorithm>
-#include <type_traits>
-
-#include <cuda_fp16.h>
-
-#include "kernels.h"
-#include "lowp.cuh"
-#include "search_core.cuh"
-
-// Rows in flight per lane group on the low-precision paths (1 or 2 16-byte
-// chunks per lane; NSG_U8ROWS row groups of NSG_U8CHUNKS chunks per lane for
-// the 8-bit form).
-#ifndef NSG_STOP_MINB
-#define NSG_STOP_MINB 3
-#endif
-#ifndef NSG_UL1
-#define NSG_UL1 2
-#endif
-#ifndef NSG_UL2
-#define NSG_UL2 2
-#endif
-#ifndef NSG_U8ROWS
-#define NSG_U8ROWS 3
-#endif
-#ifndef NSG_U8CHUNKS
-#define NSG_U8CHUNKS 2
-#endif
-#ifndef NSG_U8ROWS_WIDE
-#define NSG_U8ROWS_WIDE 8
-#endif
-#ifndef NSG_UL_WIDE
-#define NSG_UL_WIDE 4
-#endif
-#ifndef NSG_U_RERANK_WIDE
-#define NSG_U_RERANK_WIDE 3
-#endif
+#include "search_kern.cuh"
 
 namespace nsg {
-
-__host__ __device__ static inline int round32(int x) { return (x + 31) & ~31; }
-static inline int log2i(unsigned x) {
-    int r = 0;
-    while ((1u << r) < x) ++r;
-    return r;
-}
-
-struct SearchArgs {
-    const float4 *base4;  // FP32 rows [n][dp4] (re-rank and the plain form)
-    int dp4;
-    const uint4 *lowp;  // BF16 / FP8 / U8 rows [n][dc] 16-byte chunks (precision forms)
-    int dc;
-    float scale;  // query multiplier matching the low-precision copy
-    float lo;     // U8: offset of the 8-bit map
-    int rerank;   // precision forms: re-rank the final pool with FP32 rows (1),
-                  // U8 only for queries the 8-bit map rounds (2)
-    const int *adj;
-    int width, W;
-    int start;
-    const float *queries;
-    int d;
-    int64_t nq;
-    int k, L, H, hshift, max_steps, C;
-    int *ids;
-    float *d2;
-    int *n_expand, *n_dist, *status, *any_capped;
-    // learned early termination: FP16 MLP parameters (nullptr: none), logit threshold
-    const __half *stop_model;
-    float stop_logit;
-    int stop_k, stop_min_steps;
-    // trace recording: features [nq][cap][NF], change flags [nq][cap]
-    float *trace_feat;
-    unsigned char *trace_flag;
-    int trace_cap;
-    // batched uneven queries: per-query k and L (k, L above are the maxima and
-    // the output row stride is k), a visiting order and a work counter that
-    // persistent warps draw from (nullptr: static grid-stride assignment)
-    const int *kv, *Lv, *order;
-    int *work;
-    // random initial pool (count 0: start at `start`), base rows n
-    int init_count;
-    uint64_t init_seed;
-    int n;
-};
-
-// The distance functor of precision P for one query (every lane loads its
-// share of the query), handed to f.  Returns whether the 8-bit map kept
-// every query value (always true for the other forms).
-template <int G, int V, int U, int P, class F>
-__device__ __forceinline__ bool with_dist(const SearchArgs &a, const float *qp, F &&f) {
-    if constexpr (P == PREC_F32) {
-        DistF32<G, V, U> dist{{}, a.base4, a.dp4};
-        dist.Q.load(qp, a.d, a.dp4);
-        f(dist);
-        return true;
-    } else if constexpr (P == PREC_U8) {
-        // an 8-bit row is a quarter of the FP32 row: G8 lanes of up to
-        // NSG_U8CHUNKS 16-byte chunks each, 32 / G8 rows per pass
-        constexpr int VG = V * G;  // FP32 float4 capacity of a lane group
-        constexpr int G8 = VG / (4 * NSG_U8CHUNKS) < 1 ? 1 : (VG / (4 * NSG_U8CHUNKS) > 32 ? 32 : VG / (4 * NSG_U8CHUNKS));
-        constexpr int VC = VG / (4 * G8);
-        // rows of 513..1024 values run with the default register budget:
-        // more of them in flight
-        constexpr int U8R = V == 8 ? NSG_U8ROWS_WIDE : (V > 8 ? 2 : NSG_U8ROWS);
-        DistU8<G8, VC, U8R> dist{{}, a.lowp, a.dc};
-        const bool qexact = dist.Q.load(qp, a.d, a.lo, a.scale);
-        f(dist);
-        return qexact;
-    } else {
-        constexpr int VC = (V * 4) / PrecEpc<P>::value > 0 ? (V * 4) / PrecEpc<P>::value : 1;
-        // rows in flight per group: a low-precision row costs VC*4 registers per lane
-        constexpr int UL = V == 8 ? NSG_UL_WIDE : (VC <= 1 ? NSG_UL1 : (VC == 2 ? NSG_UL2 : 2));
-        DistLp<P, G, VC, UL> dist{{}, a.lowp, a.dc};
-        dist.Q.load(qp, a.d, a.scale);
-        f(dist);
-        return true;
-    }
-}
-
-// After the traversal of query qi (one warp): with `rerank` the L pool
-// entries are measured again on the FP32 rows and the k smallest of those
-// keys are kept (the re-rank list reuses the visited hash, no longer needed,
-// when it has room for k keys, else a list of its own, C = k); then the
-// results and counters are written.
-template <int G, int V, int U, int P>
-__device__ __forceinline__ void finish_query(const SearchArgs &a, WarpSmem &s, const SearchOut &o, int64_t qi,
-                                             int kq, const float *qp, bool rerank) {
-    const unsigned lane = lane_id();
-    const uint64_t *res = s.pool;
-    int rsize = o.size;
-    if constexpr (P != PREC_F32) if (rerank) {
-        uint64_t *cl = a.C > 0 ? s.clist : reinterpret_cast<uint64_t *>(s.hash);
-        // the re-rank gathers all L pool rows at once: more rows in flight
-        // than the traversal for rows of 513..1024 values
-        constexpr int UR = V == 8 ? NSG_U_RERANK_WIDE : U;
-        DistF32<G, V, UR> exact{{}, a.base4, a.dp4};
-        exact.Q.load(qp, a.d, a.dp4);
-        int kept = 0;
-        for (int c0 = 0; c0 < o.size; c0 += a.W) {
-            const int mm = o.size - c0 < a.W ? o.size - c0 : a.W;
-            for (int t = lane; t < mm; t += 32) s.ids[t] = kid(s.pool[c0 + t]);
-            __syncwarp();
-            exact(s.ids, mm, s.keys);
-            warp_merge(cl, kq, kept, s.keys, mm, s.ck, s.cp, s.sk, s.sp);
-        }
-        res = cl;
-        rsize = kept;
-    }
-    for (int c = lane; c < a.k; c += 32) {  // row stride a.k; slots past this query's k padded
-        const bool has = c < rsize && c < kq;
-        uint64_t e = has ? res[c] : KEY_INF;
-        a.ids[qi * a.k + c] = has ? kid(e) : -1;
-        if (a.d2) a.d2[qi * a.k + c] = has ? kd2(e) : __int_as_float(0x7f800000);
-    }
-    if (lane == 0) {
-        if (a.n_expand) a.n_expand[qi] = o.n_expand;
-        if (a.n_dist) a.n_dist[qi] = o.n_dist;
-        if (a.status) a.status[qi] = o.capped ? -4 : 0;
-        if (o.capped && a.any_capped) atomicOr(a.any_capped, 1);
-    }
-    __syncwarp();
-}
-
-// Alg. 1 per query, one warp each.  P = PREC_F32: distances on the FP32 rows
-// (the plain form).  P = PREC_BF16 / PREC_FP8 / PREC_U8: traversal distances
-// on the low-precision copy, then the FP32 re-rank when asked for.
-template <int G, int V, int U, int P, bool STOP>
-__device__ __forceinline__ void search_body(const SearchArgs &a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    const unsigned lane = lane_id();
-    const size_t wbytes = warp_smem_bytes(a.L, a.W, a.C, a.H);
-    WarpSmem s = carve_warp_smem(smem + warp * wbytes, a.L, a.W, a.C, a.H);
-    // the stop model lives after the warps' regions, widened to FP32
-    StopMLP *mlp = reinterpret_cast<StopMLP *>(smem + wpb * wbytes);
-    if (STOP && a.stop_model != nullptr) {
-        float *dst = reinterpret_cast<float *>(mlp);
-        for (int t = threadIdx.x; t < NSG_STOP_PARAMS; t += blockDim.x) dst[t] = __half2float(a.stop_model[t]);
-        __syncthreads();
-    }
-    int csize = 0;
-    const int64_t stride = (int64_t)gridDim.x * wpb;
-    int64_t t = (int64_t)blockIdx.x * wpb + warp;
-    for (;;) {
-        if (a.work != nullptr) {  // persistent warps draw the next query
-            int v = 0;
-            if (lane == 0) v = atomicAdd(a.work, 1);
-            t = __shfl_sync(NSG_FULL, v, 0);
-        }
-        if (t >= a.nq) break;
-        const int64_t qi = a.order != nullptr ? a.order[t] : t;
-        if (a.work == nullptr) t += stride;
-        const int kq = a.kv != nullptr ? min(max(a.kv[qi], 1), a.k) : a.k;
-        const int Lq = a.Lv != nullptr ? max(min(a.Lv[qi], a.L), kq) : a.L;
-        const float *qp = a.queries + qi * a.d;
-        StopCtx sc;
-        sc.mlp = a.stop_model != nullptr ? mlp : nullptr;
-        sc.logit = a.stop_logit;
-        sc.k = a.kv != nullptr ? min(kq, a.stop_k) : a.stop_k;
-        sc.min_steps = a.stop_min_steps;
-        sc.trace_feat = a.trace_feat != nullptr ? a.trace_feat + qi * (int64_t)a.trace_cap * NSG_STOP_NF : nullptr;
-        sc.trace_flag = a.trace_flag != nullptr ? a.trace_flag + qi * (int64_t)a.trace_cap : nullptr;
-        sc.trace_cap = a.trace_cap;
-        const StopCtx *scp = STOP ? &sc : nullptr;
-        const InitRand ir{a.init_count < Lq ? a.init_count : Lq, a.init_seed, qi, a.n};
-        const InitRand *initp = a.init_count > 0 ? &ir : nullptr;
-        SearchOut o;
-        const bool qexact = with_dist<G, V, U, P>(a, qp, [&](const auto &dist) {
-            o = warp_alg1<false, false, std::decay_t<decltype(dist)>, STOP>(
-                dist, GraphRef{a.adj, a.width}, a.start, Lq, s, (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
-                csize, nullptr, 0, scp, nullptr, initp);
-        });
-        const bool rerank = a.rerank == 1 || (P == PREC_U8 && a.rerank == 2 && !qexact);
-        finish_query<G, V, U, P>(a, s, o, qi, kq, qp, rerank);
-    }
-}
-
-// Alg. 1 per query by a group of WPQ warps that share the query's pool and
-// visited set (group_alg1): WPQ times the rows in flight per expansion, the
-// same steps and results.  Group g of a block uses named barrier 1 + g.
-struct GroupCtl {
-    int64_t t;  // the group's query (drawn by the leader)
-    int m, done;
-};
-
-template <int G, int V, int U, int P, int WPQ>
-__device__ __forceinline__ void search_group_body(const SearchArgs &a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    const int g = warp / WPQ, w = warp % WPQ, gpb = wpb / WPQ;
-    const unsigned lane = lane_id();
-    const size_t wbytes = warp_smem_bytes(a.L, a.W, a.C, a.H);
-    WarpSmem s = carve_warp_smem(smem + g * wbytes, a.L, a.W, a.C, a.H);
-    volatile GroupCtl *ctl = reinterpret_cast<volatile GroupCtl *>(smem + gpb * wbytes) + g;
-    const int bar_id = 1 + g;
-    const int64_t stride = (int64_t)gridDim.x * gpb;
-    int64_t tstat = (int64_t)blockIdx.x * gpb + g;
-    for (;;) {
-        if (w == 0 && lane == 0) ctl->t = a.work != nullptr ? (int64_t)atomicAdd(a.work, 1) : tstat;
-        tstat += stride;
-        group_bar(bar_id, 32 * WPQ);
-        const int64_t t = ctl->t;
-        if (t >= a.nq) break;  // the same value in every warp of the group
-        const int64_t qi = a.order != nullptr ? a.order[t] : t;
-        const int kq = a.kv != nullptr ? min(max(a.kv[qi], 1), a.k) : a.k;
-        const int Lq = a.Lv != nullptr ? max(min(a.Lv[qi], a.L), kq) : a.L;
-        const float *qp = a.queries + qi * a.d;
-        const InitRand ir{a.init_count < Lq ? a.init_count : Lq, a.init_seed, qi, a.n};
-        const InitRand *initp = a.init_count > 0 ? &ir : nullptr;
-        SearchOut o;
-        const bool qexact = with_dist<G, V, U, P>(a, qp, [&](const auto &dist) {
-            o = group_alg1<WPQ>(dist, GraphRef{a.adj, a.width}, a.start, Lq, s, (uint32_t)a.H - 1, a.hshift,
-                                a.max_steps, w, bar_id, ctl, initp);
-        });
-        const bool rerank = a.rerank == 1 || (P == PREC_U8 && a.rerank == 2 && !qexact);
-        if (w == 0) finish_query<G, V, U, P>(a, s, o, qi, kq, qp, rerank);
-    }
-}
-
-// Register budgets.  Rows of up to 512 values (V <= 4 float4 slices per lane)
-// are held to 4 blocks of 256 threads per SM, i.e. 64 registers and 32
-// resident warps, with no spills; left free, the low-precision kernels (which
-// also carry the FP32 re-rank) take ~112 registers and the plain one 70.
-// Wider rows (V >= 8) keep the compiler's default budget (~98), since 64 would
-// spill.  The learned-stop / trace kernels carry the feature and MLP code and
-// are held to 3 blocks per SM (rows up to 512 values) or left free (wider).
-template <int G, int V, int U, int P>
-__global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a) {
-    search_body<G, V, U, P, false>(a);
-}
-template <int G, int V, int U, int P>
-__global__ void __launch_bounds__(256) search_wide_kernel(SearchArgs a) {
-    search_body<G, V, U, P, false>(a);
-}
-template <int G, int V, int U, int P>
-__global__ void __launch_bounds__(256, NSG_STOP_MINB) search_stop_kernel(SearchArgs a) {
-    search_body<G, V, U, P, true>(a);
-}
-template <int G, int V, int U, int P>
-__global__ void __launch_bounds__(256) search_stop_wide_kernel(SearchArgs a) {
-    search_body<G, V, U, P, true>(a);
-}
-template <int G, int V, int U, int P, int WPQ>
-__global__ void __launch_bounds__(256, 4) search_group_kernel(SearchArgs a) {
-    search_group_body<G, V, U, P, WPQ>(a);
-}
-template <int G, int V, int U, int P, int WPQ>
-__global__ void __launch_bounds__(256) search_group_wide_kernel(SearchArgs a) {
-    search_group_body<G, V, U, P, WPQ>(a);
-}
-
-// Kernel for precision P at the dispatch shape G, V, U (wpq warps per query;
-// the learned-stop / trace kernels run one warp per query).
-template <int G, int V, int U, int P>
-static void (*search_entry(bool stop, int wpq))(SearchArgs) {
-    if constexpr (V <= 4) {
-        if (stop) return search_stop_kernel<G, V, U, P>;
-        if (wpq == 2) return search_group_kernel<G, V, U, P, 2>;
-        if (wpq == 4) return search_group_kernel<G, V, U, P, 4>;
-        return search_kernel<G, V, U, P>;
-    } else {
-        if (stop) return search_stop_wide_kernel<G, V, U, P>;
-        if (wpq == 2) return search_group_wide_kernel<G, V, U, P, 2>;
-        if (wpq == 4) return search_group_wide_kernel<G, V, U, P, 4>;
-        return search_wide_kernel<G, V, U, P>;
-    }
-}
 
 struct CollectArgs {
     const float4 *base4;
@@ -363,29 +60,6 @@ __global__ void __launch_bounds__(256) collect_kernel(CollectArgs a) {
     }
 }
 
-template <typename K>
-static cudaError_t config(K kernel, size_t smem_per_warp, int want_wpb, int64_t units, int *grid,
-                          int *wpb, size_t *smem, size_t smem_per_cta = 0, int step = 1) {
-    // warps per block: a multiple of `step` (the warps of one query group)
-    size_t cap = smem_optin();
-    int w = want_wpb > 0 ? want_wpb : 4;
-    w = w < step ? step : w / step * step;
-    while (w > step && smem_per_warp * w + smem_per_cta > cap) w -= step;
-    if (smem_per_warp * w + smem_per_cta > cap) return cudaErrorInvalidConfiguration;
-    *smem = smem_per_warp * w + smem_per_cta;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, w * 32, *smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    int64_t need = (units + w - 1) / w;
-    int64_t full = (int64_t)sm_count() * per_sm;
-    *grid = (int)std::max<int64_t>(1, std::min(need, full));
-    *wpb = w;
-    return cudaSuccess;
-}
-
 cudaError_t launch_search(const SearchLaunch &l, cudaStream_t st) {
     if (l.nq <= 0) return cudaSuccess;
     SearchArgs a;
@@ -430,29 +104,111 @@ cudaError_t launch_search(const SearchLaunch &l, cudaStream_t st) {
     a.init_count = l.init_count;
     a.init_seed = l.init_seed;
     a.n = (int)l.n;
-    size_t per_warp = warp_smem_bytes(a.L, a.W, a.C, a.H);
+    a.parts = l.parts > 1 && l.starts != nullptr ? l.parts : 1;
+    a.starts = l.starts;
+    a.gpool = l.gpool;
+    if (a.gpool == nullptr && a.L > 1024) return cudaErrorInvalidValue;
+    size_t per_warp = warp_smem_bytes(a.gpool != nullptr ? 0 : a.L, a.W, a.C, a.H);
     const size_t per_cta = l.stop_model ? ((sizeof(StopMLP) + 15) & ~size_t(15)) : 0;
-    cudaError_t err = cudaSuccess;
     const bool stop = l.stop_model != nullptr || l.trace_feat != nullptr;
     // warps per query: 1, 2 or 4 (the learned-stop / trace kernels use 1)
     const int wpq = stop ? 1 : (l.warps_per_query == 2 || l.warps_per_query == 4 ? l.warps_per_query : 1);
     // a group's region and its control word, spread over its warps
     if (wpq > 1) per_warp = ((per_warp + 32) / wpq + 15) & ~size_t(15);
-    NSG_DISPATCH_DP4(a.dp4, {
-        auto kern = l.precision == PREC_BF16  ? search_entry<G_, V_, U_, PREC_BF16>(stop, wpq)
-                    : l.precision == PREC_FP8 ? search_entry<G_, V_, U_, PREC_FP8>(stop, wpq)
-                    : l.precision == PREC_U8  ? search_entry<G_, V_, U_, PREC_U8>(stop, wpq)
-                                              : search_entry<G_, V_, U_, PREC_F32>(stop, wpq);
-        int grid, wpb;
-        size_t smem;
-        err = config(kern, per_warp, l.warps_per_cta, l.nq * wpq, &grid, &wpb, &smem, per_cta, wpq);
-        if (err == cudaSuccess) {
-            kern<<<grid, wpb * 32, smem, st>>>(a);
-            err = cudaGetLastError();
-        }
-    });
-    return err;
+    if (a.gpool != nullptr) return launch_search_global(a, l, per_warp, per_cta, stop, wpq, st);
+    return launch_search_args<false>(a, l, per_warp, per_cta, stop, wpq, st);
 }
+
+// Partition-and-merge (Sections 4.2, 4.3): one warp per query merges the
+// subsets' result lists into its k smallest (distance, row id) keys: each
+// list's entries are mapped to row ids and warp_merge adds them to a sorted
+// list of capacity k, one subset after the other.
+__global__ void __launch_bounds__(128) merge_parts_kernel(const int *ids_in, const float *d2_in, int64_t nq,
+                                                          int parts, int k_in, const int *perm, int k,
+                                                          int *ids_out, float *d2_out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const unsigned lane = lane_id();
+    // per warp: list [k], candidates, ck, sk [k_in] (u64); cp, sp [k_in] (int)
+    const size_t per = 8ull * (k + 3 * (size_t)k_in) + 8ull * k_in;
+    unsigned char *base = smem + warp * ((per + 15) & ~size_t(15));
+    uint64_t *list = reinterpret_cast<uint64_t *>(base);
+    uint64_t *cand = list + k;
+    uint64_t *ck = cand + k_in;
+    uint64_t *sk = ck + k_in;
+    int *cp = reinterpret_cast<int *>(sk + k_in);
+    int *sp = cp + k_in;
+    for (int64_t q = (int64_t)blockIdx.x * wpb + warp; q < nq; q += (int64_t)gridDim.x * wpb) {
+        int size = 0;
+        for (int p = 0; p < parts; ++p) {
+            const int *ir = ids_in + (q * parts + p) * (int64_t)k_in;
+            const float *dr = d2_in + (q * parts + p) * (int64_t)k_in;
+            int m = 0;
+            for (int b = 0; b < k_in; b += 32) {
+                const int j = b + (int)lane;
+                const int pos = j < k_in ? ir[j] : -1;
+                const bool has = pos >= 0;
+                const unsigned bal = __ballot_sync(NSG_FULL, has);
+                if (has) cand[m + __popc(bal & lanemask_lt())] = make_key(dr[j], perm[pos]);
+                m += __popc(bal);
+            }
+            __syncwarp();
+            if (m > 0) warp_merge(list, k, size, cand, m, ck, cp, sk, sp);
+        }
+        for (int c = lane; c < k; c += 32) {
+            const bool has = c < size;
+            ids_out[q * k + c] = has ? kid(list[c]) : -1;
+            if (d2_out) d2_out[q * k + c] = has ? kd2(list[c]) : __int_as_float(0x7f800000);
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_merge_parts(const int *ids_in, const float *d2_in, int64_t nq, int parts, int k_in,
+                               const int *perm, int k, int *ids_out, float *d2_out, cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    const size_t per = ((8ull * (k + 3 * (size_t)k_in) + 8ull * k_in) + 15) & ~size_t(15);
+    int grid, wpb;
+    size_t smem;
+    cudaError_t e = config(merge_parts_kernel, per, 4, nq, &grid, &wpb, &smem);
+    if (e != cudaSuccess) return e;
+    merge_parts_kernel<<<grid, wpb * 32, smem, st>>>(ids_in, d2_in, nq, parts, k_in, perm, k, ids_out, d2_out);
+    return cudaGetLastError();
+}
+
+__global__ void gather_rows_kernel(const float *base, int64_t n, int d, const int *perm, float *out) {
+    const int64_t total = n * d;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = x / d;
+        out[x] = base[(int64_t)perm[i] * d + (x - i * d)];
+    }
+}
+
+cudaError_t launch_gather_rows(const float *base, int64_t n, int d, const int *perm, float *out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n * d + 255) / 256, (int64_t)sm_count() * 16);
+    gather_rows_kernel<<<(int)blocks, 256, 0, st>>>(base, n, d, perm, out);
+    return cudaGetLastError();
+}
+
+__global__ void offset_adj_kernel(const int *in, int64_t total, int offset, int *out) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int v = in[x];
+        out[x] = v >= 0 ? v + offset : -1;
+    }
+}
+
+cudaError_t launch_offset_adj(const int *in, int64_t nv, int R, int offset, int *out, cudaStream_t st) {
+    if (nv <= 0) return cudaSuccess;
+    const int64_t total = nv * R;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 16);
+    offset_adj_kernel<<<(int)blocks, 256, 0, st>>>(in, total, offset, out);
+    return cudaGetLastError();
+}
+
+int64_t search_pool_slots() { return (int64_t)sm_count() * 32; }
 
 cudaError_t launch_collect(const CollectLaunch &l, cudaStream_t st) {
     if (l.nv <= 0) return cudaSuccess;

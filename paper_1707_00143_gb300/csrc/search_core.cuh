@@ -31,6 +31,17 @@
 #ifndef NSG_U_WIDE8
 #define NSG_U_WIDE8 2
 #endif
+// Software pipelining of the expansion loop (searches on a graph nobody edits
+// meanwhile): 0 off; 1 the next node's adjacency row is loaded before the
+// merge of the current expansion's keys; 2 also filtered through the visited
+// set and its new rows prefetched into L2 before the merge.  Off by default:
+// at full occupancy the search issues an instruction nearly every cycle, and
+// the prediction's extra instructions cost more than the latency they hide
+// (SIFT-shaped 1M, 10,000 queries, L = 138: 8-bit form 2.12 ms with 0, 2.39
+// with 1, 2.97 with 2; FP32 4.20 / 4.47 / 5.59 ms).
+#ifndef NSG_PIPE
+#define NSG_PIPE 0
+#endif
 
 namespace nsg {
 
@@ -156,6 +167,10 @@ struct DistF32 {
     __device__ __forceinline__ void prefetch(const int *ids, int m) const {
         if (m > U * (32 / G)) prefetch_rows_l2(base4, dp4 * 16, ids, m);
     }
+    // every row, ahead of a gather that comes later
+    __device__ __forceinline__ void prefetch_all(const int *ids, int m) const {
+        prefetch_rows_l2(base4, dp4 * 16, ids, m);
+    }
 };
 
 // Seeded random initial pool (NSG-Naive's "Alg. 1 with random
@@ -195,16 +210,22 @@ __device__ __forceinline__ int first_unchecked(const uint64_t *pool, int size, i
 // otherwise order each 32-slot load after the previous chunk's), so a row
 // costs one global round trip.
 template <bool COHERENT>
-__device__ __forceinline__ int gather_row(GraphRef g, int u, WarpSmem &s, uint32_t hmask, int hshift) {
+__device__ __forceinline__ void load_row_head(GraphRef g, int u, int (&vr)[4]) {
     const unsigned lane = lane_id();
     const int *row = g.adj + (int64_t)u * g.width;
-    int m = 0;
-    int vr[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const int slot = c * 32 + (int)lane;
         vr[c] = slot < g.width ? load_adj<COHERENT>(row + slot) : -1;
     }
+}
+
+template <bool COHERENT>
+__device__ __forceinline__ int filter_row(GraphRef g, int u, const int (&vr)[4], WarpSmem &s, uint32_t hmask,
+                                          int hshift) {
+    const unsigned lane = lane_id();
+    const int *row = g.adj + (int64_t)u * g.width;
+    int m = 0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         if (c * 32 >= g.width) break;
@@ -223,6 +244,54 @@ __device__ __forceinline__ int gather_row(GraphRef g, int u, WarpSmem &s, uint32
     }
     __syncwarp();
     return m;
+}
+
+// Reads node u's adjacency row and keeps the neighbours the visited set has
+// not seen, in row order, in s.ids; returns their count.  Warp-wide.  The
+// first 128 slots are loaded before any visit (the visited-set updates would
+// otherwise order each 32-slot load after the previous chunk's), so a row
+// costs one global round trip.
+template <bool COHERENT>
+__device__ __forceinline__ int gather_row(GraphRef g, int u, WarpSmem &s, uint32_t hmask, int hshift) {
+    int vr[4];
+    load_row_head<COHERENT>(g, u, vr);
+    return filter_row<COHERENT>(g, u, vr, s, hmask, hshift);
+}
+
+// The node Alg. 1 expands after keys[0..m) are merged into the pool, whose
+// entries up to position i are all checked: the smaller of the first
+// unchecked entry after i and the smallest new key below the tail of a full
+// pool.  ~0 when there is none.  Exact unless that new key equals a pool entry
+// (a node the visited set forgot and measured again), which the merge drops:
+// the caller checks the prediction against the merged pool.  Warp-wide.
+__device__ __forceinline__ uint64_t predict_next(const uint64_t *pool, int size, int L, int i, const uint64_t *keys,
+                                                 int m) {
+    const unsigned lane = lane_id();
+    const uint64_t tail = size >= L ? kval(pool[L - 1]) : ~0ull;
+    uint64_t best = ~0ull;
+    for (int j = (int)lane; j < m; j += 32) {
+        const uint64_t k = keys[j];
+        if (k < tail && k < best) best = k;
+    }
+    const int c = first_unchecked(pool, size, i + 1);
+    if (c >= 0 && lane == 0) {
+        const uint64_t o = kval(pool[c]);
+        if (o < best) best = o;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t x = __shfl_xor_sync(NSG_FULL, best, o);
+        best = x < best ? x : best;
+    }
+    return best;
+}
+
+// Takes back the visited-set claims of ids[0..m) (a speculative row filter
+// for a node that is not expanded next): the set then has forgotten them,
+// which only costs a recomputation, never a skipped node.  Warp-wide.
+__device__ __forceinline__ void unvisit_all(WarpSmem &s, uint32_t hmask, int hshift, int m) {
+    for (int j = (int)lane_id(); j < m; j += 32) unvisit(s.hash, hmask, hshift, s.ids[j]);
+    __syncwarp();
 }
 
 // The initial pool: the start node, or the set of `init->count` seeded
@@ -343,11 +412,22 @@ __device__ SearchOut group_alg1(const D &dist, GraphRef g, int start, int L, War
 
 // `dist(ids, m, keys)` writes keys[c] = (d2(query, row ids[c]), ids[c]) for c < m.
 // STOP: compile the learned-stop / trace hooks (stop must then be non-null).
+//
+// Pipelining (NSG_PIPE, graphs nobody edits during the search): once the keys
+// of an expansion are known, the node Alg. 1 expands next is predicted
+// (predict_next) and its adjacency row is read -- with NSG_PIPE 2 also
+// filtered through the visited set, its new rows prefetched into L2 -- before
+// the keys are merged into the pool, so those memory round trips overlap the
+// merge.  After the merge the first unchecked entry is found as always; when
+// it is the predicted node the prepared row is used, otherwise (rare: see
+// predict_next) the speculative visited-set claims are taken back and the
+// row is read again.  The steps, keys and results are those of the plain loop.
 template <bool COLLECT, bool COHERENT, class D, bool STOP = false>
 __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, WarpSmem &s, uint32_t hmask,
                                int hshift, int max_steps, int excl, int C, int &csize, int *xlog = nullptr,
                                int xcap = 0, const StopCtx *stop = nullptr, uint64_t *xthr = nullptr,
                                const InitRand *init = nullptr) {
+    constexpr int PIPE = COHERENT ? 0 : NSG_PIPE;
     const unsigned lane = lane_id();
     SearchOut o;
     o.size = 0;
@@ -360,6 +440,9 @@ __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, Warp
     init_pool(dist, start, L, s, hmask, hshift, init, o);
     if (COLLECT && (init == nullptr || init->count <= 0)) collect_merge(s, 1, excl, C, csize);
     int cursor = 0;
+    int pre_u = -1;  // node whose row is prepared (PIPE)
+    int pre_m = 0;   // PIPE 2: its new neighbours, already in s.ids
+    int vr[4];       // PIPE 1: its first 128 adjacency slots
     for (;;) {
         const int i = first_unchecked(s.pool, o.size, cursor);
         if (i < 0) break;
@@ -408,10 +491,19 @@ __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, Warp
             // only below the L-th key (anything, while the pool is not full)
             if (xthr != nullptr) xthr[o.n_expand - 1] = o.size < L ? KEY_INF : kval(s.pool[L - 1]);
         }
-        const int m = gather_row<COHERENT>(g, u, s, hmask, hshift);
+        int m;
+        if (PIPE == 2 && u == pre_u) {
+            m = pre_m;  // filtered before the previous merge
+        } else if (PIPE == 1 && u == pre_u) {
+            m = filter_row<COHERENT>(g, u, vr, s, hmask, hshift);
+        } else {
+            if (PIPE == 2 && pre_u >= 0) unvisit_all(s, hmask, hshift, pre_m);  // mispredicted
+            m = gather_row<COHERENT>(g, u, s, hmask, hshift);
+        }
+        pre_u = -1;
         last_m = m;
 #if NSG_PF_ROWS
-        if (m > 0) dist.prefetch(s.ids, m);
+        if (m > 0 && PIPE != 2) dist.prefetch(s.ids, m);
 #endif
         if (m == 0) {
             cursor = i + 1;
@@ -426,6 +518,20 @@ __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, Warp
         dist(s.ids, m, s.keys);
         o.n_dist += m;
         if (COLLECT) collect_merge(s, m, excl, C, csize);
+        if constexpr (PIPE != 0) {
+            const uint64_t nx = predict_next(s.pool, o.size, L, i, s.keys, m);
+            if (nx != ~0ull && o.n_expand < max_steps) {
+                pre_u = kid(nx);
+                if constexpr (PIPE == 2) {
+                    // s.ids is free: the keys carry their ids
+                    __syncwarp();
+                    pre_m = gather_row<COHERENT>(g, pre_u, s, hmask, hshift);
+                    if (pre_m > 0) dist.prefetch_all(s.ids, pre_m);
+                } else {
+                    load_row_head<COHERENT>(g, pre_u, vr);
+                }
+            }
+        }
         int lo = warp_merge(s.pool, L, o.size, s.keys, m, s.ck, s.cp, s.sk, s.sp);
         cursor = min(i + 1, lo);
         if constexpr (STOP) {  // did this expansion change the first k entries?
@@ -435,6 +541,9 @@ __device__ SearchOut warp_alg1(const D &dist, GraphRef g, int start, int L, Warp
                 stop->trace_flag[o.n_expand - 1] = last_changed ? 1 : 0;
         }
     }
+    // a row prepared for a node that was never expanded (the search ended):
+    // its claims leave the visited set, which callers may still consult
+    if (PIPE == 2 && pre_u >= 0) unvisit_all(s, hmask, hshift, pre_m);
     __syncwarp();
     return o;
 }
