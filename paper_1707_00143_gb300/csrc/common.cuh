@@ -297,19 +297,36 @@ __device__ __forceinline__ int warp_merge(uint64_t *list, int cap, int &size, co
     }
     __syncwarp();
     if (nk == 0) return cap;
-    // rank among the kept candidates (stable on equal keys)
+    // rank among the kept candidates (stable on equal keys): the number of
+    // smaller keys plus the number of equal keys before it
     bool dup = false;
-    for (int j = lane; j < nk; j += 32) {
-        uint64_t k = ck[j];
+    if (nk <= 32) {
+        // one candidate per lane; equal keys (the same node offered twice)
+        // found with one match instruction instead of a second compare per key
+        const uint64_t k = (int)lane < nk ? ck[lane] : ~0ull;  // ~0: no key
         int r = 0;
-        for (int i = 0; i < nk; ++i) {
-            uint64_t o = ck[i];
-            const bool same_before = o == k && i < j;
-            r += (o < k) || same_before;
-            dup |= same_before;
+#pragma unroll 4
+        for (int i = 0; i < nk; ++i) r += ck[i] < k;
+        const int before = __popc(__match_any_sync(NSG_FULL, k) & lanemask_lt());
+        if ((int)lane < nk) {
+            r += before;
+            dup = before > 0;
+            sk[r] = k;
+            sp[r] = cp[lane];
         }
-        sk[r] = k;
-        sp[r] = cp[j];
+    } else {
+        for (int j = lane; j < nk; j += 32) {
+            uint64_t k = ck[j];
+            int r = 0;
+            for (int i = 0; i < nk; ++i) {
+                uint64_t o = ck[i];
+                const bool same_before = o == k && i < j;
+                r += (o < k) || same_before;
+                dup |= same_before;
+            }
+            sk[r] = k;
+            sp[r] = cp[j];
+        }
     }
     __syncwarp();
     if (__any_sync(NSG_FULL, dup)) {
