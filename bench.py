@@ -97,7 +97,7 @@ def parse():
     p.add_argument("--naive", action="store_true", help="also build and sweep NSG-Naive (ablation)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the partition-and-merge and nn-descent legs")
-    p.add_argument("--profile-case", choices=["search", "knn", "build"], default=None,
+    p.add_argument("--profile-case", choices=["search", "knn", "build", "nndescent", "partitioned"], default=None,
                    help="run one kernel family on a small SIFT-shaped case for a profiler")
     p.add_argument("--n", type=int, default=300000, help="--profile-case: base rows")
     p.add_argument("--nq", type=int, default=2000, help="--profile-case: queries")
@@ -287,15 +287,19 @@ def cpu_alg1(adj, deg, base, nav, q, k, L, budget_s=8.0):
 
     cores = os.cpu_count() or 1
 
+    counts = {}
+
     def run(qs, nt):
-        oracle.search(adj, base, nav, qs, k, L, deg=deg, nthreads=nt)
+        _, _, ne, nd = oracle.search(adj, base, nav, qs, k, L, deg=deg, nthreads=nt)
+        counts["n_expand"], counts["n_dist"] = ne, nd
 
     m1, el1 = _timed_sample(lambda qs: run(qs, 1), q, budget_s / 2, 2000)
     m, el = _timed_sample(lambda qs: run(qs, cores), q, budget_s, len(q))
-    return {"value": m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"oracle Alg. 1 (k = {k}, L = {L}) over the first {m} queries on {cores} host threads, "
-                      f"on the index the library built",
-            "single_thread": {"value": m1 / el1, "queries": m1}}
+    out = {"value": m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"oracle Alg. 1 (k = {k}, L = {L}) over the first {m} queries on {cores} host threads, "
+                     f"on the index the library built",
+           "single_thread": {"value": m1 / el1, "queries": m1}}
+    return out, counts
 
 
 def profile_case(args):
@@ -303,7 +307,10 @@ def profile_case(args):
     builds an index (K=100, L=40, R=50, C=500) on an n-row base and runs
     `--reps` searches of nq queries (top 100, pool --L) in the precision form
     --prec with --wpq warps per query; `knn` runs one brute-force kNN graph
-    (K = --K); `build` one index construction."""
+    (K = --K); `build` one index construction; `nndescent` one nn-descent
+    kNN graph (K = --K, 16 samples and 16 reverse samples, 12 iterations);
+    `partitioned` a 4-subset partitioned index and `--reps` partitioned
+    searches (top 100, pool --L)."""
     import torch
 
     from paper_1707_00143_gb300 import build as nsg_build_mod
@@ -317,6 +324,21 @@ def profile_case(args):
         capi.nsg_knn_init(bt, args.K, with_d2=False)
         torch.cuda.synchronize()
         print(f"knn n={args.n} K={args.K} done")
+        return
+    if args.profile_case == "nndescent":
+        _, _, it, upd = capi.nsg_knn_nndescent(bt, args.K, capi.NnDescentParams(16, 16, 12, 0.001, 1), with_d2=False)
+        torch.cuda.synchronize()
+        print(f"nndescent n={args.n} K={args.K} iterations={it} last_updates={upd} done")
+        return
+    if args.profile_case == "partitioned":
+        pidx = capi.nsg_build_partitioned(bt, datagen.even_partition(args.n, 4, seed=17), 100, 40, 50, 500)
+        if args.prec:
+            pidx.prepare(args.prec)
+        prm = capi.SearchParams(0, 0, args.prec, 0, -1)
+        for _ in range(args.reps):
+            pidx.search_partitioned(qt, 100, args.L, params=prm)
+        torch.cuda.synchronize()
+        print(f"partitioned n={args.n} nq={args.nq} L={args.L} prec={args.prec} done")
         return
     idx = capi.nsg_build(bt, 100, 40, 50, 500)
     if args.profile_case == "build":
@@ -765,6 +787,28 @@ def main():
     extras = {} if args.no_extras else extra_legs(capi, datagen, bt, qt, gt, base, W, forms, chosen_form, nq, kq,
                                                    recall10, ev0, ev1, st, args)
 
+    # CPU baseline: the oracle's Alg. 1 on this index; its unique expansion and
+    # distance counts are the algorithmic counts of the roofline where it
+    # covered the whole batch (the GPU counting pass is checked against them)
+    cpu, count_src = None, "GPU counting pass (16,384-slot visited set)"
+    counts_check = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        adj_h, deg_h = (t.cpu().numpy() for t in idx.graph())
+        cpu, oc = cpu_alg1(adj_h, deg_h, base, info["nav"], q, kc, L)
+        cpu["serial_scan"] = cpu_serial_scan(base, q)
+        del adj_h, deg_h
+        if base_form == "plain" or info["has_" + base_form] == 2:  # the oracle takes the same steps
+            mq = len(oc["n_expand"])
+            g_ne = cnt["n_expand"][:mq].cpu().numpy()
+            g_nd = cnt["n_dist"][:mq].cpu().numpy()
+            counts_check = {"queries": mq, "n_expand_equal": float((g_ne == oc["n_expand"]).mean()),
+                            "n_dist_equal": float((g_nd == oc["n_dist"]).mean())}
+            if mq == nq and "+stop" not in chosen_form:
+                n_expand, n_dist = int(oc["n_expand"].sum()), int(oc["n_dist"].sum())
+                bytes_launch = (n_dist * row_bytes + n_expand * R * 4 + nq * (d * 4 + kc * 8)
+                                + (nq * L * d * 4 if lossy else 0))
+                count_src = "oracle Alg. 1 on the same index and queries"
+
     peak, peak_kind = peaks()
     achieved = bytes_launch / (ms_step / 1e3) / 1e9
     src = kernel_source_hash()
@@ -795,12 +839,6 @@ def main():
     rec_held = capi.nsg_recall(o_held["ids"][:, :10].contiguous(), gt_held, 10).sum().item() / (10.0 * nq)
     del qht, gt_held, o_held
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        adj_h, deg_h = (t.cpu().numpy() for t in idx.graph())
-        cpu = cpu_alg1(adj_h, deg_h, base, info["nav"], q, kc, L)
-        cpu["serial_scan"] = cpu_serial_scan(base, q)
-        del adj_h, deg_h
 
     if rank == 0:
         line = {
@@ -830,7 +868,8 @@ def main():
                       "fixup_edges": info["n_fixup_edges"], "fixup_researched": info["n_fixup_searches"],
                       "nav": info["nav"], "bf16_exact": info["has_bf16"] == 2, "u8_exact": info["has_u8"] == 2,
                       "fp8_scale": info["fp8_scale"]},
-            "per_query": {"n_expand": n_expand / nq, "n_dist": n_dist / nq},
+            "per_query": {"n_expand": n_expand / nq, "n_dist": n_dist / nq, "source": count_src,
+                          "gpu_counting_pass_vs_oracle": counts_check},
             "batched": batched,
             "partitioned": extras.get("partitioned"),
             "nndescent": extras.get("nndescent"),

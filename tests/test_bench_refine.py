@@ -53,7 +53,11 @@ def test_cpu_alg1_baseline_on_an_oracle_graph():
 
     base, q = datagen.workload("tiny", n=2000, nq=64)
     ref = oracle.build(base, 16, 30, 12, 100, seed=0)
-    out = bench.cpu_alg1(ref["adj"], ref["deg"], base, ref["nav"], q, 10, 40, budget_s=0.2)
+    out, counts = bench.cpu_alg1(ref["adj"], ref["deg"], base, ref["nav"], q, 10, 40, budget_s=0.2)
+    # the counts of the all-thread sample are the oracle's own
+    m = len(counts["n_expand"])
+    _, _, ne, nd = oracle.search(ref["adj"], base, ref["nav"], q[:m], 10, 40, deg=ref["deg"])
+    assert np.array_equal(counts["n_expand"], ne) and np.array_equal(counts["n_dist"], nd)
     assert out["kind"] == "oracle" and out["unit"] == bench.UNIT
     assert out["value"] > 0 and out["single_thread"]["value"] > 0
     assert out["cores"] >= 1 and "Alg. 1" in out["sample"]

@@ -107,6 +107,13 @@ def test_knn_wide_float_rows(nsg, n, d, k):
     # distance beyond rounding, and the sets agree
     assert (exact <= rd2[:, -1:].astype(np.float64) * (1 + 1e-5)).all()
     assert oracle.recall(ids, rid, k) >= 0.995
+    # and every row is a valid answer: k distinct existing rows, never itself,
+    # in ascending distance -- with the bound above, k rows none of which is
+    # farther than the true k-th neighbour
+    assert ((ids >= 0) & (ids < n)).all()
+    assert all(len(set(row.tolist())) == k for row in ids)
+    assert not (ids == np.arange(n)[:, None]).any()
+    assert (np.diff(d2, axis=1) >= 0).all()
 
 
 def test_knn_query_gist_shaped(nsg):
