@@ -136,12 +136,32 @@ inline unsigned next_pow2(unsigned x) {
     while (p < x) p <<= 1;
     return p;
 }
-// Visited-set slots per query.  Small on purpose: the set may forget (results
-// do not change), and 2 KB per warp keeps 28 warps resident per SM; measured
-// on the 1M x 128 workload, 512 slots beat 1024 and 2048 at L = 100..200.
+// Visited-set slots per query of the build's searches (collect, connectivity).
+// Small on purpose: the set may forget (results do not change), and 2 KB per
+// warp keeps the build kernels' occupancy.
 inline int default_hash(int L, int width) {
     (void)width;
     return L <= 1024 ? 512 : 2048;  // longer searches measure more nodes
+}
+
+// Visited-set slots per query of nsg_search / nsg_search_ex: 1024 when the
+// searches still hold 32 warps per SM with it (the search kernels keep the
+// merge's sorted keys in the candidate keys' space), else 512.  Measured on
+// the SIFT-shaped 1M at L = 138 (10,000 queries): 1024 slots re-measure 9 %
+// fewer nodes and run 2-3 % faster than 512 in every form; where 1024 slots
+// cost resident warps (L = 150 and up at R = 50) they are slower.
+inline int default_search_hash(int L, int width) {
+    if (L > 1024) return 2048;
+    static int smem_sm = 0, reserved = 0;
+    if (!smem_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    }
+    const int W = (width + 31) & ~31;
+    const size_t per_block = 4 * nsg::search_warp_smem_bytes(L, W, 1024) + (size_t)reserved;
+    return smem_sm > 0 && 8 * per_block <= (size_t)smem_sm ? 1024 : 512;
 }
 inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -944,7 +964,7 @@ nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t n
     l.nq = nq;
     l.k = k;
     l.L = L;
-    l.hash_slots = p.hash_slots > 0 ? p.hash_slots : default_hash(L, idx->R);
+    l.hash_slots = p.hash_slots > 0 ? p.hash_slots : default_search_hash(L, idx->R);
     l.max_steps = p.max_steps > 0 ? p.max_steps : nsg::default_steps(L);
     l.warps_per_cta = p.warps_per_cta;
     l.ids = ids_dev;
@@ -1433,7 +1453,7 @@ nsg_status nsg_search(const nsg_index *idx, const float *queries_dev, int64_t nq
     l.nq = nq;
     l.k = k;
     l.L = L;
-    l.hash_slots = default_hash(L, idx->R);
+    l.hash_slots = default_search_hash(L, idx->R);
     l.max_steps = nsg::default_steps(L);
     l.warps_per_cta = 0;
     l.ids = ids_dev;

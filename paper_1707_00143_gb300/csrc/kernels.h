@@ -88,6 +88,9 @@ cudaError_t launch_nndescent(const NnDescentLaunch &l, cudaStream_t st);
 // on the global-memory pool slots a launch uses (the search kernels hold at
 // most 32 warps per SM).
 int64_t search_pool_slots();
+// Shared memory per warp of the fixed-L search kernels (pool of L keys in
+// shared memory, adjacency width rounded to W, H visited slots, no re-rank list).
+size_t search_warp_smem_bytes(int L, int W, int H);
 cudaError_t launch_search(const SearchLaunch &a, cudaStream_t st);
 
 // Partition-and-merge: per query, the union of `parts` sorted result lists

@@ -108,7 +108,7 @@ cudaError_t launch_search(const SearchLaunch &l, cudaStream_t st) {
     a.starts = l.starts;
     a.gpool = l.gpool;
     if (a.gpool == nullptr && a.L > 1024) return cudaErrorInvalidValue;
-    size_t per_warp = warp_smem_bytes(a.gpool != nullptr ? 0 : a.L, a.W, a.C, a.H);
+    size_t per_warp = warp_smem_bytes(a.gpool != nullptr ? 0 : a.L, a.W, a.C, a.H, true);
     const size_t per_cta = l.stop_model ? ((sizeof(StopMLP) + 15) & ~size_t(15)) : 0;
     const bool stop = l.stop_model != nullptr || l.trace_feat != nullptr;
     // warps per query: 1, 2 or 4 (the learned-stop / trace kernels use 1)
@@ -209,6 +209,8 @@ cudaError_t launch_offset_adj(const int *in, int64_t nv, int R, int offset, int 
 }
 
 int64_t search_pool_slots() { return (int64_t)sm_count() * 32; }
+
+size_t search_warp_smem_bytes(int L, int W, int H) { return warp_smem_bytes(L, W, 0, H, true); }
 
 cudaError_t launch_collect(const CollectLaunch &l, cudaStream_t st) {
     if (l.nv <= 0) return cudaSuccess;

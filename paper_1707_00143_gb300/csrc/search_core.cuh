@@ -57,21 +57,26 @@ struct WarpSmem {
     int *sp;          // [W]
 };
 
-__host__ __device__ inline size_t warp_smem_bytes(int L, int W, int C, int H) {
-    size_t b = 8ull * (L + 3 * W + C) + 4ull * (H + 3 * W);
+// SHARE_SK: the merge's sorted-key scratch shares the candidate keys' space.
+// warp_merge reads its candidates only before it writes sk, so this holds
+// wherever one merge consumes the keys -- not in collect mode, where the
+// same keys feed the collect list's merge and then the pool's.  The bytes
+// saved let the searches hold a larger visited set at full occupancy.
+__host__ __device__ inline size_t warp_smem_bytes(int L, int W, int C, int H, bool share_sk = false) {
+    size_t b = 8ull * (L + (share_sk ? 2 : 3) * W + C) + 4ull * (H + 3 * W);
     return (b + 15) & ~size_t(15);
 }
 
 // Layout per warp: hash first (16-byte aligned for the vector clear; H is a
 // power of two >= 4), then the 8-byte arrays, then the int arrays.
-__device__ inline WarpSmem carve_warp_smem(unsigned char *p, int L, int W, int C, int H) {
+__device__ inline WarpSmem carve_warp_smem(unsigned char *p, int L, int W, int C, int H, bool share_sk = false) {
     WarpSmem s;
     s.hash = reinterpret_cast<uint32_t *>(p);
     s.pool = reinterpret_cast<uint64_t *>(s.hash + H);
     s.keys = s.pool + L;
     s.ck = s.keys + W;
-    s.sk = s.ck + W;
-    s.clist = s.sk + W;
+    s.sk = share_sk ? s.keys : s.ck + W;
+    s.clist = s.ck + (share_sk ? 1 : 2) * W;
     s.ids = reinterpret_cast<int *>(s.clist + C);
     s.cp = s.ids + W;
     s.sp = s.cp + W;

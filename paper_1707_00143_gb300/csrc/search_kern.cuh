@@ -189,8 +189,8 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
     const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const unsigned lane = lane_id();
     const int Ls = GP ? 0 : a.L;  // pool keys held in shared memory
-    const size_t wbytes = warp_smem_bytes(Ls, a.W, a.C, a.H);
-    WarpSmem s = carve_warp_smem(smem + warp * wbytes, Ls, a.W, a.C, a.H);
+    const size_t wbytes = warp_smem_bytes(Ls, a.W, a.C, a.H, true);
+    WarpSmem s = carve_warp_smem(smem + warp * wbytes, Ls, a.W, a.C, a.H, true);
     if constexpr (GP) s.pool = a.gpool + ((int64_t)blockIdx.x * wpb + warp) * a.L;
     // the stop model lives after the warps' regions, widened to FP32
     StopMLP *mlp = reinterpret_cast<StopMLP *>(smem + wpb * wbytes);
@@ -252,8 +252,8 @@ __device__ __forceinline__ void search_group_body(const SearchArgs &a) {
     const int g = warp / WPQ, w = warp % WPQ, gpb = wpb / WPQ;
     const unsigned lane = lane_id();
     const int Ls = GP ? 0 : a.L;
-    const size_t wbytes = warp_smem_bytes(Ls, a.W, a.C, a.H);
-    WarpSmem s = carve_warp_smem(smem + g * wbytes, Ls, a.W, a.C, a.H);
+    const size_t wbytes = warp_smem_bytes(Ls, a.W, a.C, a.H, true);
+    WarpSmem s = carve_warp_smem(smem + g * wbytes, Ls, a.W, a.C, a.H, true);
     if constexpr (GP) s.pool = a.gpool + ((int64_t)blockIdx.x * gpb + g) * a.L;
     volatile GroupCtl *ctl = reinterpret_cast<volatile GroupCtl *>(smem + gpb * wbytes) + g;
     const int bar_id = 1 + g;
