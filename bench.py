@@ -240,13 +240,17 @@ def kernel_source_hash(files=SEARCH_SOURCES):
 # profiles/search_kernel_u8_sift.md has the capture.  A source change changes
 # the hash, and `traffic` is null until re-measured.
 NCU_TRAFFIC = {
-    ("ae7f3d5fded47695", "sift", "u8", 150): (1_668_171_264 + 10_440_960) / 10_000,
-    ("ae7f3d5fded47695", "sift", "u8", 138): (1_539_700_992 + 10_233_600) / 10_000,
+    ("95c42f7aed64dad1", "sift", "u8", 138): (1_515_921_664 + 16_310_272) / 10_000,
+}
+# warp instructions of one search launch, per query (smsp__inst_executed.sum of the
+# same capture command with that metric), keyed like NCU_TRAFFIC: the issue roofline
+NCU_INSTRUCTIONS = {
+    ("95c42f7aed64dad1", "sift", "u8", 138): 1_369_312_578 / 10_000,
 }
 # the same for the MRNG edge selection of the build, per node, keyed by
 # (source hash, workload): profiles/prune_kernel_sift1m.md
 PRUNE_TRAFFIC = {
-    ("dc4dfdd243843fcb", "sift"): (18_540_747_008 + 134_831_616 + 16_068_677_120 + 113_730_048) / 1_000_000,
+    ("ac51e03d3f24d394", "sift"): (18_539_054_336 + 134_604_800 + 16_068_004_352 + 113_740_800) / 1_000_000,
 }
 
 
@@ -802,7 +806,8 @@ def main():
             g_ne = cnt["n_expand"][:mq].cpu().numpy()
             g_nd = cnt["n_dist"][:mq].cpu().numpy()
             counts_check = {"queries": mq, "n_expand_equal": float((g_ne == oc["n_expand"]).mean()),
-                            "n_dist_equal": float((g_nd == oc["n_dist"]).mean())}
+                            "n_dist_equal": float((g_nd == oc["n_dist"]).mean()),
+                            "n_dist_gpu_over_oracle": float(g_nd.sum() / max(1, oc["n_dist"].sum()))}
             if mq == nq and "+stop" not in chosen_form:
                 n_expand, n_dist = int(oc["n_expand"].sum()), int(oc["n_dist"].sum())
                 bytes_launch = (n_dist * row_bytes + n_expand * R * 4 + nq * (d * 4 + kc * 8)
@@ -817,6 +822,20 @@ def main():
                 "frac": achieved / peak, "traffic": (tr * nq if tr else None),
                 "peak_kind": peak_kind, "kernel": f"search_kernel ({chosen_form})",
                 "algorithmic_bytes": bytes_launch, "kernel_src": src}
+    # instruction issue: the search kernel is bound by it (ncu: ~73 % of active cycles
+    # issue); warp instructions per launch over its time, against one instruction per
+    # cycle per scheduler (4 per SM) at the maximum SM clock
+    ins = NCU_INSTRUCTIONS.get((src, args.workload, chosen_form, L))
+    issue_roofline = None
+    if ins:
+        props = torch.cuda.get_device_properties(0)
+        mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", 2070.0) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 2070.0
+        ipeak = props.multi_processor_count * 4 * mhz * 1e6
+        iach = ins * nq / (ms_step / 1e3)
+        issue_roofline = {"bound": "issue", "achieved": iach, "peak": ipeak, "unit": "warp instructions/s",
+                          "frac": iach / ipeak, "instructions_per_query": ins, "kernel_src": src,
+                          "peak_from": "SMs x 4 schedulers x max SM clock"}
     # MRNG edge selection over the whole build: every examined candidate's id,
     # distance and FP32 row read once, the adjacency row, degree and candidate
     # count per node; over the prune launches' CUDA-event time
@@ -854,6 +873,7 @@ def main():
                       "recall10": rec_plain},
             "chosen_over_plain": ms_plain / ms_step,
             "roofline": roofline,
+            "issue_roofline": issue_roofline,
             "prune_roofline": prune_roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": job_qps(world, nq, e2e_ms), "unit": UNIT,
