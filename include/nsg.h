@@ -165,8 +165,10 @@ nsg_status nsg_knn_query(const float *base_dev, int64_t n, int32_t d, const floa
  *   (entries not in it before are flagged new).  It stops after `iters`
  *   iterations or once an iteration changes at most delta * n * K entries.
  *   The result depends on the inputs alone; on integer data it equals the
- *   CPU oracle's bit for bit.  Recall against the exact graph is the
- *   caller's to measure.
+ *   CPU oracle's bit for bit (integer data spanning at most 256 values with
+ *   d * 255^2 < 2^24 are measured on an 8-bit copy of the rows made for the
+ *   call: the same exact distances, a quarter of the bytes).  Recall against
+ *   the exact graph is the caller's to measure.
  * nsg_knn_nndescent: knn_ids_dev [n][K] i32 out, knn_d2_dev [n][K] f32 out
  *   (nullable), sorted by key; iters_run / last_updates (host, nullable).
  *   1 <= K < n, K <= 256.  Allocates scratch; synchronises once per

@@ -242,12 +242,43 @@ bool nndescent_params_ok(const nsg_nndescent_params &p) {
 }
 
 // Approximate kNN graph by nn-descent into ids [n][K] (d2 nullable), with
-// scratch allocated for the call.  base [n][dp] padded rows.
-nsg_status nndescent_run(const float *base, int64_t n, int dp, int K, const nsg_nndescent_params &p, int *ids,
-                         float *d2, int *iters_run, int64_t *last_updates, cudaStream_t st) {
-    DevBuf<unsigned char> scratch;
+// scratch allocated for the call.  base [n][dp] padded rows of d values.
+// Integer data of span <= 255 with d * 255^2 < 2^24 (every distance an exact
+// integer below 2^24) get an 8-bit copy x - min for the distances: the same
+// keys as the FP32 rows at a quarter of the bytes gathered.
+nsg_status nndescent_run(const float *base, int64_t n, int dp, int d, int K, const nsg_nndescent_params &p,
+                         int *ids, float *d2, int *iters_run, int64_t *last_updates, cudaStream_t st) {
+    DevBuf<unsigned char> scratch, u8;
     NSG_CK(scratch.alloc(nsg::nndescent_scratch_bytes(n, K, p.sample, p.reverse)));
+    float lo = 0.0f;
+    bool use_u8 = false;
+    const int dpl = (d + 15) / 16 * 16;
+    if ((int64_t)d * 65025 < (1 << 24)) {
+        DevBuf<unsigned> flags;
+        NSG_CK(flags.alloc(4));
+        unsigned mm[3] = {0xffffffffu, 0u, 0u};
+        NSG_CK(cudaMemcpyAsync(flags.p, mm, sizeof(mm), cudaMemcpyHostToDevice, st));
+        NSG_CK(nsg::launch_minmax(base, n, dp, d, flags.p, st));
+        NSG_CK(cudaMemcpyAsync(mm, flags.p, sizeof(mm), cudaMemcpyDeviceToHost, st));
+        NSG_CK(cudaStreamSynchronize(st));
+        const float mn = nsg::float_from_order_key(mm[0]), mx = nsg::float_from_order_key(mm[1]);
+        if (mm[2] == 0 && (double)mx - (double)mn <= 255.0) {
+            lo = mn;
+            NSG_CK(cudaMemsetAsync(flags.p, 0, sizeof(unsigned), st));
+            NSG_CK(u8.alloc((size_t)n * dpl));
+            NSG_CK(nsg::launch_to_lowp(base, n, dp, d, NSG_PREC_U8, 1.0f, lo, u8.p, dpl,
+                                       reinterpret_cast<int *>(flags.p), st));
+            unsigned inexact = 0;
+            NSG_CK(cudaMemcpyAsync(&inexact, flags.p, sizeof(inexact), cudaMemcpyDeviceToHost, st));
+            NSG_CK(cudaStreamSynchronize(st));
+            use_u8 = inexact == 0;
+        }
+    }
     nsg::NnDescentLaunch l;
+    l.u8 = use_u8 ? u8.p : nullptr;
+    l.u8_chunks = dpl / 16;
+    l.u8_lo = lo;
+    l.d = d;
     l.base = base;
     l.n = n;
     l.dp = dp;
@@ -695,7 +726,7 @@ static nsg_status build_index(const float *base_dev, int64_t n, int32_t d, int32
     // A1: kNN graph, exact or by nn-descent
     auto t0 = std::chrono::steady_clock::now();
     if (!s && !nnd) s = knn_run(base.p, n, ix->dp, base.p, n, 0, K, 1, knn.p, nullptr, st);
-    if (!s && nnd) s = nndescent_run(base.p, n, ix->dp, K, *nnd, knn.p, nullptr, &ix->knn_iters, nullptr, st);
+    if (!s && nnd) s = nndescent_run(base.p, n, ix->dp, d, K, *nnd, knn.p, nullptr, &ix->knn_iters, nullptr, st);
     if (!s && (e = cudaStreamSynchronize(st)) != cudaSuccess) s = cuda_fail(e, "knn");
     ix->ms[0] = (float)since_ms(t0);
     // A2 + A3: centroid and navigating node
@@ -767,7 +798,7 @@ nsg_status nsg_knn_nndescent(const float *base_dev, int64_t n, int32_t d, int32_
         if (s) return s;
         int it = 0;
         int64_t upd = 0;
-        s = nndescent_run(view, n, round_up4(d), K, *params, knn_ids_dev, knn_d2_dev, &it, &upd, st);
+        s = nndescent_run(view, n, round_up4(d), d, K, *params, knn_ids_dev, knn_d2_dev, &it, &upd, st);
         if (s) return s;
         if (iters_run) *iters_run = it;
         if (last_updates) *last_updates = upd;

@@ -80,6 +80,11 @@ struct NnDescentLaunch {
     void *scratch;
     int *iters_run;         // host, nullable
     int64_t *last_updates;  // host, nullable
+    // an 8-bit copy of the rows (x - u8_lo, u8_chunks 16-byte chunks per row)
+    // that holds every distance exactly, or nullptr; d = the row's values
+    const void *u8 = nullptr;
+    int u8_chunks = 0, d = 0;
+    float u8_lo = 0.0f;
 };
 size_t nndescent_scratch_bytes(int64_t n, int K, int S, int Sr);
 cudaError_t launch_nndescent(const NnDescentLaunch &l, cudaStream_t st);

@@ -25,6 +25,7 @@
 #include <algorithm>
 
 #include "kernels.h"
+#include "lowp.cuh"
 #include "search_core.cuh"
 
 namespace nsg {
@@ -84,11 +85,37 @@ struct NdArgs {
     const int64_t *moff;    // [n + 1]
     int *members;           // (v << 1) | (p in NEW(v))
     unsigned long long *updates;
+    // 8-bit copy (rows of dc 16-byte chunks, x - lo) when it holds every
+    // distance exactly, else nullptr: distances on FP32 rows
+    const uint4 *u8;
+    int dc, d;
+    float lo;
 };
+
+// The distance functor for node v's row as the query: FP32 rows, or the exact
+// 8-bit copy (a quarter of the bytes, the same keys), laid out as the 8-bit
+// search form lays it out (lanes of 2 16-byte chunks, 3 row groups in flight;
+// 8 for rows of 513..1024 values).
+template <int G, int V, int U, bool U8, class F>
+__device__ __forceinline__ void nd_with_dist(const NdArgs &a, int64_t v, F &&f) {
+    if constexpr (U8) {
+        constexpr int VG = V * G;
+        constexpr int G8 = VG / 8 < 1 ? 1 : (VG / 8 > 32 ? 32 : VG / 8);
+        constexpr int VC = VG / (4 * G8);
+        constexpr int R8 = V == 8 ? 8 : (V > 8 ? 2 : 3);
+        DistU8<G8, VC, R8> dist{{}, a.u8, a.dc};
+        dist.Q.load(reinterpret_cast<const float *>(a.base4 + v * a.dp4), a.d, a.lo, 1.0f);
+        f(dist);
+    } else {
+        DistF32<G, V, U> dist{{}, a.base4, a.dp4};
+        dist.Q.load_row(a.base4 + v * a.dp4, a.dp4);
+        f(dist);
+    }
+}
 
 // init: K distinct seeded random neighbours per node, sorted by key.  One warp
 // per node: lane 0 draws, the warp checks each draw against the ids so far.
-template <int G, int V, int U>
+template <int G, int V, int U, bool U8>
 __global__ void __launch_bounds__(128) nd_init_kernel(NdArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -110,16 +137,16 @@ __global__ void __launch_bounds__(128) nd_init_kernel(NdArgs a) {
                 ++m;
             }
         }
-        DistF32<G, V, U> dist{{}, a.base4, a.dp4};
-        dist.Q.load_row(a.base4 + v * a.dp4, a.dp4);
         int size = 0;
-        for (int c0 = 0; c0 < a.K; c0 += ND_W) {
-            const int cnt = min(ND_W, a.K - c0);
-            for (int j = lane; j < cnt; j += 32) s.ids[j] = got[c0 + j];
-            __syncwarp();
-            dist(s.ids, cnt, s.keys);
-            warp_merge(s.list, a.K, size, s.keys, cnt, s.ck, s.cp, s.sk, s.sp);
-        }
+        nd_with_dist<G, V, U, U8>(a, v, [&](const auto &dist) {
+            for (int c0 = 0; c0 < a.K; c0 += ND_W) {
+                const int cnt = min(ND_W, a.K - c0);
+                for (int j = lane; j < cnt; j += 32) s.ids[j] = got[c0 + j];
+                __syncwarp();
+                dist(s.ids, cnt, s.keys);
+                warp_merge(s.list, a.K, size, s.keys, cnt, s.ck, s.cp, s.sk, s.sp);
+            }
+        });
         for (int j = lane; j < a.K; j += 32) a.lists[v * a.K + j] = s.list[j];  // all new
         __syncwarp();
     }
@@ -273,7 +300,7 @@ __global__ void nd_member_fill_kernel(NdArgs a) {
 // The offers to p (NEW(v) u OLD(v) for members v with p in NEW(v), NEW(v)
 // for the others), the ones the visited set has not seen measured, and p's
 // list cut to its K smallest keys of itself and them.
-template <int G, int V, int U>
+template <int G, int V, int U, bool U8>
 __global__ void __launch_bounds__(128) nd_join_kernel(NdArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -293,37 +320,38 @@ __global__ void __launch_bounds__(128) nd_join_kernel(NdArgs a) {
         __syncwarp();
         if (lane == 0) visit(s.hash, hmask, hshift, (int)p);
         __syncwarp();
-        DistF32<G, V, U> dist{{}, a.base4, a.dp4};
-        dist.Q.load_row(a.base4 + p * a.dp4, a.dp4);
-        int size = a.K, m = 0;
-        const int64_t m0 = a.moff[p], m1 = a.moff[p + 1];
-        for (int64_t mi = m0; mi < m1; ++mi) {
-            const int tag = a.members[mi];
-            const int64_t v = tag >> 1;
-            const int cn = a.cNEW[v], co = (tag & 1) ? a.cOLD[v] : 0;
-            for (int b = 0; b < cn + co; b += 32) {
-                const int j = b + (int)lane;
-                const int x = j < cn ? a.NEWs[v * W2 + j] : (j < cn + co ? a.OLDs[v * W2 + j - cn] : -1);
-                // p itself is among its own offers (p is in NEW(v)); the visited set
-                // may have forgotten it, so it is excluded by id
-                const bool fresh = x >= 0 && x != (int)p && visit(s.hash, hmask, hshift, x);
-                const unsigned bal = __ballot_sync(NSG_FULL, fresh);
-                const int cnt = __popc(bal);
-                if (m + cnt > ND_W) {  // flush the batch first
+        int size = a.K;
+        nd_with_dist<G, V, U, U8>(a, p, [&](const auto &dist) {
+            int m = 0;
+            const int64_t m0 = a.moff[p], m1 = a.moff[p + 1];
+            for (int64_t mi = m0; mi < m1; ++mi) {
+                const int tag = a.members[mi];
+                const int64_t v = tag >> 1;
+                const int cn = a.cNEW[v], co = (tag & 1) ? a.cOLD[v] : 0;
+                for (int b = 0; b < cn + co; b += 32) {
+                    const int j = b + (int)lane;
+                    const int x = j < cn ? a.NEWs[v * W2 + j] : (j < cn + co ? a.OLDs[v * W2 + j - cn] : -1);
+                    // p itself is among its own offers (p is in NEW(v)); the visited set
+                    // may have forgotten it, so it is excluded by id
+                    const bool fresh = x >= 0 && x != (int)p && visit(s.hash, hmask, hshift, x);
+                    const unsigned bal = __ballot_sync(NSG_FULL, fresh);
+                    const int cnt = __popc(bal);
+                    if (m + cnt > ND_W) {  // flush the batch first
+                        __syncwarp();
+                        dist(s.ids, m, s.keys);
+                        warp_merge(s.list, a.K, size, s.keys, m, s.ck, s.cp, s.sk, s.sp);
+                        m = 0;
+                    }
+                    if (fresh) s.ids[m + __popc(bal & lanemask_lt())] = x;
+                    m += cnt;
                     __syncwarp();
-                    dist(s.ids, m, s.keys);
-                    warp_merge(s.list, a.K, size, s.keys, m, s.ck, s.cp, s.sk, s.sp);
-                    m = 0;
                 }
-                if (fresh) s.ids[m + __popc(bal & lanemask_lt())] = x;
-                m += cnt;
-                __syncwarp();
             }
-        }
-        if (m > 0) {
-            dist(s.ids, m, s.keys);
-            warp_merge(s.list, a.K, size, s.keys, m, s.ck, s.cp, s.sk, s.sp);
-        }
+            if (m > 0) {
+                dist(s.ids, m, s.keys);
+                warp_merge(s.list, a.K, size, s.keys, m, s.ck, s.cp, s.sk, s.sp);
+            }
+        });
         // entries that were not in the list at the iteration's start
         int changed = 0;
         for (int j = lane; j < a.K; j += 32) {
@@ -461,6 +489,10 @@ cudaError_t launch_nndescent(const NnDescentLaunch &l, cudaStream_t st) {
     a.S = S;
     a.Sr = Sr;
     a.seed = l.seed;
+    a.u8 = reinterpret_cast<const uint4 *>(l.u8);
+    a.dc = l.u8_chunks;
+    a.d = l.d;
+    a.lo = l.u8_lo;
     a.lists = reinterpret_cast<uint64_t *>(take(8ull * n * K));
     a.newS = reinterpret_cast<uint64_t *>(take(8ull * n * std::max(S, 1)));
     a.oldS = reinterpret_cast<uint64_t *>(take(8ull * n * std::max(S, 1)));
@@ -488,7 +520,11 @@ cudaError_t launch_nndescent(const NnDescentLaunch &l, cudaStream_t st) {
     const size_t per_warp = (nd_warp_bytes(K) + 15) & ~size_t(15);
     cudaError_t e = cudaSuccess;
     const int dp4 = a.dp4;
-    NSG_DISPATCH_DP4(dp4, { e = warp_launch(nd_init_kernel<G_, V_, U_>, a, per_warp, st); });
+    const bool u8 = a.u8 != nullptr;
+    NSG_DISPATCH_DP4(dp4, {
+        e = u8 ? warp_launch(nd_init_kernel<G_, V_, U_, true>, a, per_warp, st)
+               : warp_launch(nd_init_kernel<G_, V_, U_, false>, a, per_warp, st);
+    });
     if (e != cudaSuccess) return e;
     int it = 0;
     unsigned long long upd = 0;
@@ -508,7 +544,10 @@ cudaError_t launch_nndescent(const NnDescentLaunch &l, cudaStream_t st) {
         if ((e = exclusive_scan(a.mcnt, n, moff, bsum, st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(a.mcnt, 0, 4ull * n, st)) != cudaSuccess) return e;
         nd_member_fill_kernel<<<grid_for(n * std::max(W2, 1), 256), 256, 0, st>>>(a);
-        NSG_DISPATCH_DP4(dp4, { e = warp_launch(nd_join_kernel<G_, V_, U_>, a, per_warp, st); });
+        NSG_DISPATCH_DP4(dp4, {
+            e = u8 ? warp_launch(nd_join_kernel<G_, V_, U_, true>, a, per_warp, st)
+                   : warp_launch(nd_join_kernel<G_, V_, U_, false>, a, per_warp, st);
+        });
         if (e != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(&upd, a.updates, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
