@@ -74,9 +74,12 @@ typedef struct {
                               splitmix64(init_seed + q * 0x9e3779b97f4a7c15 + j) mod n,
                               j < init_random (NSG-Naive's random initialisation) */
     uint64_t init_seed;
-    int32_t warps_per_query; /* 1 (default), 2 or 4 warps share each query: the same
-                                steps and results, more rows in flight per expansion
-                                (not with a stop model or a trace) */
+    int32_t warps_per_query; /* 1, 2 or 4 warps share each query: the same steps and
+                                results, more rows in flight per expansion (not with a
+                                stop model or a trace, which run 1).  0 auto: for FP32
+                                rows of more than 2 KB 4 (L <= 1024) or 2; else 1 above
+                                L = 1024, and 4, 2 or 1 as the batch leaves each SM fewer
+                                than 2, fewer than 8, or more queries */
     int32_t pool;          /* where each query's pool of L keys lives: 0 auto (shared memory
                               up to L = 1024, global memory above), 1 shared memory
                               (L <= 1024), 2 global memory (L <= NSG_MAX_L: one L2-resident
@@ -84,7 +87,24 @@ typedef struct {
                               for nsg_plan_create -- and grown on demand; calls with global
                               pools on one index on different streams at once race on it).
                               The same steps and results either way. */
+    int32_t stage_rows;    /* how a warp gathers the base rows it measures, for rows of more
+                              than 512 values (d > 512): 0 auto, < 0 through registers (a few
+                              rows in flight per warp), 1..NSG_STAGE_MAX staged: each warp
+                              copies up to that many rows at once into a ring of shared-memory
+                              slots with the bulk-copy (TMA) engine and measures them there
+                              (fewer where one query's warps would not fit in a block).
+                              Auto stages traversal rows of more than 2 KB (FP32 rows of more
+                              than 512 values) with 4 slots: bulk copies of rows picked at
+                              random complete about one after another, so staging beats the
+                              register gather only where that gather holds few rows.  The
+                              same steps and results either way.  Staging
+                              is refused (NSG_EINVAL) for d <= 512 and with a stop model or a
+                              trace.  A staged copy that has not landed after 4 s (a fault,
+                              never expected) ends its warp's queries with status NSG_ECUDA. */
 } nsg_search_params;
+
+/* Most rows a staged gather holds in flight per warp (nsg_search_params.stage_rows). */
+#define NSG_STAGE_MAX 32
 
 /* Largest pool size L of any search (global-memory pools; 1024 in shared memory). */
 #define NSG_MAX_L 8192
@@ -306,7 +326,8 @@ nsg_status nsg_index_from_graph(const float *base_dev, int64_t n, int32_t d, con
  *   on one index may be in flight on different streams at once.
  * nsg_search_ex: same with parameters and optional per-query outputs
  *   n_expand_dev [nq] (nodes checked), n_dist_dev [nq] (distances computed),
- *   status_dev [nq] (0 or NSG_ESTEPCAP).  Does not synchronise.
+ *   status_dev [nq] (0, NSG_ESTEPCAP, or NSG_ECUDA for a staged copy that
+ *   never landed, see stage_rows).  Does not synchronise.
  *   params->precision BF16 / FP8 (after nsg_index_prepare): traversal
  *   distances on that copy with FP32 accumulation; with re-rank, the L pool
  *   entries are measured again on the FP32 rows and the k smallest returned
@@ -398,6 +419,7 @@ typedef struct {
     float worst_ms;        /* slowest shape tried */
     int32_t warps_per_query; /* chosen warps per query */
     int32_t pool;          /* chosen pool placement: 1 shared memory, 2 global memory */
+    int32_t stage_rows;    /* chosen staged-gather slots per warp (0: register gathers) */
 } nsg_plan_info_t;
 
 nsg_status nsg_search_batched(const nsg_index *idx, const float *queries_dev, int64_t nq, const int32_t *k_dev,

@@ -35,19 +35,20 @@ class SearchParams(C.Structure):
                 ("warps_per_cta", C.c_int32), ("rerank", C.c_int32), ("stop_model", C.c_void_p),
                 ("stop_threshold", C.c_float), ("stop_k", C.c_int32), ("stop_min_steps", C.c_int32),
                 ("init_random", C.c_int32), ("init_seed", C.c_uint64), ("warps_per_query", C.c_int32),
-                ("pool", C.c_int32)]
+                ("pool", C.c_int32), ("stage_rows", C.c_int32)]
 
     def __init__(self, max_steps=0, hash_slots=0, precision=0, warps_per_cta=0, rerank=-1, stop_model=None,
-                 stop_threshold=0.5, stop_k=0, stop_min_steps=0, init_random=0, init_seed=0, warps_per_query=1,
-                 pool=0):
+                 stop_threshold=0.5, stop_k=0, stop_min_steps=0, init_random=0, init_seed=0, warps_per_query=0,
+                 pool=0, stage_rows=0):
         ptr = stop_model.data_ptr() if isinstance(stop_model, torch.Tensor) else stop_model
         super().__init__(max_steps, hash_slots, precision, warps_per_cta, rerank, ptr, stop_threshold, stop_k,
-                         stop_min_steps, init_random, init_seed, warps_per_query, pool)
+                         stop_min_steps, init_random, init_seed, warps_per_query, pool, stage_rows)
 
 
 STOP_FEATURES, STOP_PARAMS = 8, 641
 POOL_AUTO, POOL_SHARED, POOL_GLOBAL = 0, 1, 2
 MAX_L = 8192
+STAGE_MAX = 32  # staged row gathers: most rows in flight per warp (SearchParams.stage_rows)
 
 
 class NnDescentParams(C.Structure):
@@ -381,7 +382,7 @@ class Index:
 class PlanInfo(C.Structure):
     _fields_ = [("warps_per_cta", C.c_int32), ("hash_slots", C.c_int32), ("n_tried", C.c_int32),
                 ("best_ms", C.c_float), ("worst_ms", C.c_float), ("warps_per_query", C.c_int32),
-                ("pool", C.c_int32)]
+                ("pool", C.c_int32), ("stage_rows", C.c_int32)]
 
 
 class Plan:

@@ -488,6 +488,15 @@ size_t smem_optin() {
     return cache[dev] > 0 ? (size_t)cache[dev] : 48 * 1024;
 }
 
+size_t smem_per_sm() {
+    static int cache[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cache[dev]) cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    return cache[dev] > 0 ? (size_t)cache[dev] : 64 * 1024;
+}
+
 }  // namespace nsg
 
 extern "C" {
@@ -966,10 +975,12 @@ nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t n
                        int32_t *n_dist_dev, int32_t *status_dev, nsg::SearchLaunch &l) {
     if (!idx || k < 1 || L < k || L > NSG_MAX_L || nq < 0 || nq >= INT32_MAX) return NSG_EINVAL;
     if (nq > 0 && (!queries_dev || !ids_dev)) return NSG_EINVAL;
-    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0, 0, 0, 1, 0};
+    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0, 0, 0, 0, 0, 0};
     if (params) p = *params;
     if (p.pool < 0 || p.pool > 2 || (p.pool == 1 && L > 1024)) return NSG_EINVAL;
     l.pool_global = p.pool == 2 || (p.pool == 0 && L > 1024);
+    if (p.stage_rows > NSG_STAGE_MAX || (p.stage_rows > 0 && (idx->dp <= 512 || p.stop_model))) return NSG_EINVAL;
+    l.stage = p.stage_rows == 0 ? -1 : (p.stage_rows < 0 ? 0 : p.stage_rows);
     if (p.precision < NSG_PREC_F32 || p.precision > NSG_PREC_U8) return NSG_EINVAL;
     if (p.init_random < 0 || p.init_random > L) return NSG_EINVAL;
     if (p.warps_per_query != 0 && p.warps_per_query != 1 && p.warps_per_query != 2 && p.warps_per_query != 4)
@@ -1006,7 +1017,7 @@ nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t n
     l.any_capped = nullptr;
     l.init_count = p.init_random;
     l.init_seed = p.init_seed;
-    l.warps_per_query = p.warps_per_query > 1 ? p.warps_per_query : 1;
+    l.warps_per_query = p.warps_per_query > 0 ? p.warps_per_query : nsg::search_auto_wpq(nq, idx->dp, p.precision, L);
     if (p.precision != NSG_PREC_F32) {
         l.precision = p.precision;
         l.lowp = idx->lowp[p.precision];
@@ -1169,7 +1180,7 @@ nsg_status nsg_search_host(const nsg_index *idx, const float *queries_host, int6
     if (e == cudaSuccess) e = se;
     if (s) return s;
     if (e != cudaSuccess) return cuda_fail(e, "nsg_search_host");
-    return capped ? NSG_ESTEPCAP : NSG_OK;
+    return (capped & 2) ? NSG_ECUDA : capped ? NSG_ESTEPCAP : NSG_OK;  // bit 1: a staged copy never landed
 }
 
 }  // extern "C"
@@ -1296,7 +1307,7 @@ nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best = 1e30f, worst = 0.0f;
-        int bw = 0, bh = 0, bq = 1, tried = 0;
+        int bw = 0, bh = 0, bq = 1, tried = 0, bs = p->l.stage;
         uint64_t *bp = p->l.gpool;
         const bool groups_ok = p->l.stop_model == nullptr;  // the stop kernels run one warp per query
         // pool placement: shared memory where L fits (<= 1024) unless the caller
@@ -1304,6 +1315,15 @@ nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64
         std::vector<uint64_t *> pools;
         if (!p->l.pool_global) pools.push_back(nullptr);
         if (p->gpool) pools.push_back(p->gpool);
+        // row gathers: registers and (rows of more than 512 values) staged,
+        // unless the caller fixed them
+        std::vector<int> stages;
+        if (params && params->stage_rows != 0) stages.push_back(p->l.stage);
+        else {
+            stages.push_back(0);
+            if (p->l.dp > 512 && groups_ok) stages.push_back(-1);
+        }
+        for (int sg : stages)
         for (uint64_t *gp : pools)
         for (int q : {1, 2, 4})
             for (int w : {2, 4, 8})
@@ -1314,6 +1334,8 @@ nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64
                 t.hash_slots = h;
                 t.warps_per_query = q;
                 t.gpool = gp;
+                t.stage = sg;
+                if (sg < 0 && nsg::search_stage_resolve(t) == 0) continue;  // auto resolves to registers
                 if (batched_run(t, st) || cudaStreamSynchronize(st) != cudaSuccess) continue;
                 cudaEventRecord(e0, st);
                 bool ok = true;
@@ -1331,6 +1353,7 @@ nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64
                     bh = h;
                     bq = q;
                     bp = gp;
+                    bs = sg;
                 }
             }
         cudaEventDestroy(e0);
@@ -1340,6 +1363,7 @@ nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64
             p->l.hash_slots = bh;
             p->l.warps_per_query = bq;
             p->l.gpool = bp;
+            p->l.stage = bs;
             p->info.best_ms = best;
             p->info.worst_ms = worst;
         }
@@ -1349,6 +1373,7 @@ nsg_status nsg_plan_create(const nsg_index *idx, const float *queries_dev, int64
     p->info.hash_slots = p->l.hash_slots;
     p->info.warps_per_query = p->l.warps_per_query;
     p->info.pool = p->l.gpool ? 2 : 1;
+    p->info.stage_rows = nsg::search_stage_resolve(p->l);
     // capture "reset counter + search" once; a run replays it
     s = batched_run(p->l, st);  // sets kernel attributes outside the capture
     cudaError_t e = cudaStreamSynchronize(st);
@@ -1391,7 +1416,7 @@ nsg_status nsg_search_trace(const nsg_index *idx, const float *queries_dev, int6
                             const nsg_search_params *params, int32_t *ids_dev, float *feat_dev,
                             uint8_t *flag_dev, int32_t *steps_dev, int32_t cap, void *stream) {
     if (cap < 1 || (nq > 0 && (!feat_dev || !flag_dev || !steps_dev))) return NSG_EINVAL;
-    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0, 0, 0, 1, 0};
+    nsg_search_params p = {0, 0, NSG_PREC_F32, 0, -1, nullptr, 0.5f, 0, 0, 0, 0, 1, 0, 0};
     if (params) p = *params;
     p.stop_model = nullptr;  // traces record the fixed-L search
     nsg::SearchLaunch l;
@@ -1493,13 +1518,15 @@ nsg_status nsg_search(const nsg_index *idx, const float *queries_dev, int64_t nq
     l.n_dist = nullptr;
     l.status = nullptr;
     l.any_capped = idx->flag;
+    l.stage = -1;  // staged row gathers where they pay (FP32 rows of more than 2 KB)
+    l.warps_per_query = nsg::search_auto_wpq(nq, idx->dp, NSG_PREC_F32, L);
     l.pool_global = L > 1024;
     NSG_CK(cudaMemsetAsync(idx->flag, 0, sizeof(int), st));
     if (nsg_status ls = launch_dynamic(idx, l, st)) return ls;
     int h = 0;
     NSG_CK(cudaMemcpyAsync(&h, idx->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     NSG_CK(cudaStreamSynchronize(st));
-    return h ? NSG_ESTEPCAP : NSG_OK;
+    return (h & 2) ? NSG_ECUDA : h ? NSG_ESTEPCAP : NSG_OK;  // bit 1: a staged copy never landed
 }
 
 nsg_status nsg_recall(const int32_t *ids_dev, int32_t ld_ids, const int32_t *gt_dev, int32_t ld_gt,

@@ -63,6 +63,10 @@ struct SearchLaunch {
     int pool_global = 0;
     uint64_t *gpool = nullptr;
     int64_t gpool_slots = 0;
+    // staged row gathers for rows of more than 512 values (stage.cuh): 0 off,
+    // > 0 that many slots per warp (at most 32), < 0 chosen by the launch
+    // (search_stage_slots)
+    int stage = 0;
 };
 // Approximate kNN graph by nn-descent (nndescent.cu).  base [n][dp] padded
 // rows; ids [n][K] out, d2 [n][K] out (nullable); scratch: at least
@@ -95,6 +99,15 @@ cudaError_t launch_nndescent(const NnDescentLaunch &l, cudaStream_t st);
 int64_t search_pool_slots();
 // Shared memory per warp of the fixed-L search kernels (pool of L keys in
 // shared memory, adjacency width rounded to W, H visited slots, no re-rank list).
+// Slots per warp the launch gives the staged gathers of rows of `row_bytes`
+// when `stage` < 0 (0: the register gather).
+int search_stage_slots(int row_bytes);
+// Warps per query when the caller leaves them to the library: `units` search
+// units (queries, or query-subset pairs) with pools of L keys on rows of `dp`
+// padded values in traversal precision `precision`.
+int search_auto_wpq(int64_t units, int dp, int precision, int L);
+// Slots per warp launch_search gives the staged gathers of `l` (0: none).
+int search_stage_resolve(const SearchLaunch &l);
 size_t search_warp_smem_bytes(int L, int W, int H);
 cudaError_t launch_search(const SearchLaunch &a, cudaStream_t st);
 
@@ -234,5 +247,6 @@ void record_cuda_error(cudaError_t e, const char *what);
 // Device properties cached per device.
 int sm_count();
 size_t smem_optin();
+size_t smem_per_sm();
 
 }  // namespace nsg

@@ -103,6 +103,29 @@ struct DistU8 {
     __device__ __forceinline__ void prefetch_all(const int *ids, int m) const {
         prefetch_rows_l2(base, dc * 16, ids, m);
     }
+    // staged gathers: the register gather's arithmetic on a shared-memory row
+    __device__ __forceinline__ const void *row_addr(int id) const { return base + (int64_t)id * dc; }
+    __device__ __forceinline__ int row_bytes() const { return dc * 16; }
+    __device__ __forceinline__ float row_smem(const unsigned char *row) const {
+        const uint4 *r = reinterpret_cast<const uint4 *>(row);
+        const int sub = lane_id() % G;
+        unsigned s = 0;
+#pragma unroll
+        for (int t = 0; t < VC; ++t) {
+            const int k = t * G + sub;
+            const uint4 x = k < dc ? r[k] : make_uint4(0, 0, 0, 0);
+            const uint32_t a[4] = {x.x, x.y, x.z, x.w};
+            const uint32_t b[4] = {Q.q[t].x, Q.q[t].y, Q.q[t].z, Q.q[t].w};
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const unsigned df = __vabsdiffu4(a[w], b[w]);
+                s = __dp4a(df, df, s);
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(NSG_FULL, s, o, G);
+        return (float)s;
+    }
 };
 
 template <int P>
@@ -209,6 +232,26 @@ struct DistLp {
     // every row, ahead of a gather that comes later
     __device__ __forceinline__ void prefetch_all(const int *ids, int m) const {
         prefetch_rows_l2(base, dc * 16, ids, m);
+    }
+    // staged gathers: the register gather's arithmetic on a shared-memory row
+    __device__ __forceinline__ const void *row_addr(int id) const { return base + (int64_t)id * dc; }
+    __device__ __forceinline__ int row_bytes() const { return dc * 16; }
+    __device__ __forceinline__ float row_smem(const unsigned char *row) const {
+        const uint4 *r = reinterpret_cast<const uint4 *>(row);
+        const int sub = lane_id() % G;
+        float s = 0.0f;
+#pragma unroll
+        for (int t = 0; t < VC; ++t) {
+            const int k = t * G + sub;
+            float f[EPC];
+            unpack<P>(k < dc ? r[k] : make_uint4(0, 0, 0, 0), f);
+#pragma unroll
+            for (int e = 0; e < EPC; ++e) {
+                const float df = f[e] - Q.q[t][e];
+                s = fmaf(df, df, s);
+            }
+        }
+        return group_sum<G>(s);
     }
 };
 

@@ -115,8 +115,63 @@ cudaError_t launch_search(const SearchLaunch &l, cudaStream_t st) {
     const int wpq = stop ? 1 : (l.warps_per_query == 2 || l.warps_per_query == 4 ? l.warps_per_query : 1);
     // a group's region and its control word, spread over its warps
     if (wpq > 1) per_warp = ((per_warp + 32) / wpq + 15) & ~size_t(15);
+    // staged row gathers: rows of more than 512 values, without the stop kernels
+    a.stage_nb = 0;
+    a.stage_rb = 0;
+    if (l.stage > 0 && (stop || a.dp4 <= 128)) return cudaErrorInvalidValue;
+    const int nb = search_stage_resolve(l);
+    if (nb > 0) {
+        a.stage_nb = nb;
+        a.stage_rb = (l.precision == PREC_F32 ? a.dp4 : a.dc) * 16;
+        const size_t pw = per_warp + stage_bytes(nb, a.stage_rb);
+        return a.gpool != nullptr ? launch_search_staged_global(a, l, pw, wpq, st)
+                                  : launch_search_staged(a, l, pw, wpq, st);
+    }
     if (a.gpool != nullptr) return launch_search_global(a, l, per_warp, per_cta, stop, wpq, st);
     return launch_search_args<false>(a, l, per_warp, per_cta, stop, wpq, st);
+}
+
+// Slots per warp of the staged gathers launch_search uses for `l` (0: the
+// register gather).
+int search_stage_resolve(const SearchLaunch &l) {
+    const bool stop = l.stop_model != nullptr || l.trace_feat != nullptr;
+    const int dp4 = l.dp / 4;
+    if (l.stage == 0 || stop || dp4 <= 128) return 0;
+    const int wpq = l.warps_per_query == 2 || l.warps_per_query == 4 ? l.warps_per_query : 1;
+    const bool rerank = l.precision != PREC_F32 && l.rerank;
+    const int C = rerank && (size_t)l.hash_slots * 4 < (size_t)l.k * 8 ? l.k : 0;
+    size_t per_warp = warp_smem_bytes(l.gpool != nullptr ? 0 : l.L, round32(l.width), C, l.hash_slots, true);
+    if (wpq > 1) per_warp = ((per_warp + 32) / wpq + 15) & ~size_t(15);
+    const int rb = (l.precision == PREC_F32 ? dp4 : l.lowp_chunks) * 16;
+    int nb = l.stage > 0 ? std::min(l.stage, STAGE_MAX_SLOTS) : search_stage_slots(rb);
+    // a block holds at least one query's warps: fewer slots where those would not fit
+    while (nb > 1 && (size_t)wpq * (per_warp + stage_bytes(nb, rb)) > smem_optin()) --nb;
+    return nb;
+}
+
+// Auto staging, as measured on the GIST-shaped 1M x 960 search (k = 100,
+// L = 300): bulk copies of rows picked at random complete about one after
+// another (~0.4 us each, nearly whatever the row's size), so staging pays
+// only where the register gather itself is slow -- FP32 rows of more than
+// 2 KB, two in flight per lane group -- and there a ring of 4 slots beats
+// larger ones (the ring costs occupancy).
+int search_stage_slots(int row_bytes) { return row_bytes > 2048 ? 4 : 0; }
+
+// Warps per query, as measured on the GIST-shaped 1M x 960 search and the
+// SIFT-shaped 1M x 128 one.  A group of warps shortens each expansion (more
+// rows in flight) but holds more warps per query: it pays while the batch
+// leaves the SMs short of warps, and while the pool is small enough to stay
+// in shared memory (a group's leader merges into a global-memory pool while
+// its other warps wait).  1,000 GIST-shaped queries (6.6 per SM), 8-bit rows:
+// L = 300 2 warps 307 k queries/s, 1 warp 234 k; L = 1,059 1 warp 54.7 k,
+// 2 warps 43.5 k.  FP32 rows of more than 2 KB (two in flight per lane group
+// in registers): 4 warps at L <= 600 (109 k against 89 k at L = 300), 2 above.
+// 2,500 SIFT-shaped queries (16 per SM): 1 warp 2.53 M, 2 warps 1.52 M.
+int search_auto_wpq(int64_t units, int dp, int precision, int L) {
+    if (precision == PREC_F32 && dp * 4 > 2048) return L <= 1024 ? 4 : 2;
+    if (L > 1024) return 1;
+    const int64_t per_sm = (units + sm_count() - 1) / sm_count();
+    return per_sm < 2 ? 4 : per_sm < 8 ? 2 : 1;
 }
 
 // Partition-and-merge (Sections 4.2, 4.3): one warp per query merges the

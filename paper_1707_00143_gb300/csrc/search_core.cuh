@@ -176,6 +176,22 @@ struct DistF32 {
     __device__ __forceinline__ void prefetch_all(const int *ids, int m) const {
         prefetch_rows_l2(base4, dp4 * 16, ids, m);
     }
+    // Staged gathers (stage.cuh): where row `id` lives, its bytes, and the
+    // distance to a copy of it in shared memory -- the lanes' slices and the
+    // order of the sums are those of the register gather, so are the keys.
+    __device__ __forceinline__ const void *row_addr(int id) const { return base4 + (int64_t)id * dp4; }
+    __device__ __forceinline__ int row_bytes() const { return dp4 * 16; }
+    __device__ __forceinline__ float row_smem(const unsigned char *row) const {
+        const float4 *r = reinterpret_cast<const float4 *>(row);
+        const int sub = lane_id() % G;
+        float s = 0.0f;
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+            const int k = t * G + sub;
+            s += sq4(k < dp4 ? r[k] : make_float4(0.f, 0.f, 0.f, 0.f), Q.q[t]);
+        }
+        return group_sum<G>(s);
+    }
 };
 
 // Seeded random initial pool (NSG-Naive's "Alg. 1 with random

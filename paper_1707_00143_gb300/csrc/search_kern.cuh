@@ -10,6 +10,7 @@
 #include "kernels.h"
 #include "lowp.cuh"
 #include "search_core.cuh"
+#include "stage.cuh"
 
 // Rows in flight per lane group on the low-precision paths (1 or 2 16-byte
 // chunks per lane; NSG_U8ROWS row groups of NSG_U8CHUNKS chunks per lane for
@@ -89,6 +90,9 @@ struct SearchArgs {
     const int *starts;
     // global-memory pools: slot (block, warp or group) of L keys, or nullptr
     uint64_t *gpool;
+    // staged row gathers (stage.cuh): slots per warp and bytes per slot of
+    // each warp's ring, which follows the warps' (groups') regions
+    int stage_nb, stage_rb;
 };
 
 // Query row and start node of search unit t.
@@ -105,12 +109,24 @@ __device__ __forceinline__ int64_t unit_query(const SearchArgs &a, int64_t t, in
 // The distance functor of precision P for one query (every lane loads its
 // share of the query), handed to f.  Returns whether the 8-bit map kept
 // every query value (always true for the other forms).
-template <int G, int V, int U, int P, class F>
-__device__ __forceinline__ bool with_dist(const SearchArgs &a, const float *qp, F &&f) {
+template <bool ST, class D, class F>
+__device__ __forceinline__ void run_dist(const D &dist, const StageRef *sr, F &&f) {
+    if constexpr (ST) {
+        const DistStaged<D> sd{dist, *sr, stage_slots(dist, *sr), dist.row_bytes()};
+        f(sd);
+    } else {
+        f(dist);
+    }
+}
+
+// ST: the rows are gathered through the warp's staging ring *sr (the host
+// sizes it for at least one traversal row).
+template <int G, int V, int U, int P, bool ST = false, class F>
+__device__ __forceinline__ bool with_dist(const SearchArgs &a, const float *qp, const StageRef *sr, F &&f) {
     if constexpr (P == PREC_F32) {
         DistF32<G, V, U> dist{{}, a.base4, a.dp4};
         dist.Q.load(qp, a.d, a.dp4);
-        f(dist);
+        run_dist<ST>(dist, sr, f);
         return true;
     } else if constexpr (P == PREC_U8) {
         // an 8-bit row is a quarter of the FP32 row: G8 lanes of up to
@@ -123,7 +139,7 @@ __device__ __forceinline__ bool with_dist(const SearchArgs &a, const float *qp, 
         constexpr int U8R = V == 8 ? NSG_U8ROWS_WIDE : (V > 8 ? 2 : NSG_U8ROWS);
         DistU8<G8, VC, U8R> dist{{}, a.lowp, a.dc};
         const bool qexact = dist.Q.load(qp, a.d, a.lo, a.scale);
-        f(dist);
+        run_dist<ST>(dist, sr, f);
         return qexact;
     } else {
         constexpr int VC = (V * 4) / PrecEpc<P>::value > 0 ? (V * 4) / PrecEpc<P>::value : 1;
@@ -131,7 +147,7 @@ __device__ __forceinline__ bool with_dist(const SearchArgs &a, const float *qp, 
         constexpr int UL = V == 8 ? NSG_UL_WIDE : (VC <= 1 ? NSG_UL1 : (VC == 2 ? NSG_UL2 : 2));
         DistLp<P, G, VC, UL> dist{{}, a.lowp, a.dc};
         dist.Q.load(qp, a.d, a.scale);
-        f(dist);
+        run_dist<ST>(dist, sr, f);
         return true;
     }
 }
@@ -141,9 +157,12 @@ __device__ __forceinline__ bool with_dist(const SearchArgs &a, const float *qp, 
 // keys are kept (the re-rank list reuses the visited hash, no longer needed,
 // when it has room for k keys, else a list of its own, C = k); then the
 // results and counters are written.
-template <int G, int V, int U, int P>
+// ST: the re-rank gathers its FP32 rows through the staging ring when at
+// least one fits there, and a staged copy that never landed (the ring's
+// failure word) makes the query's status NSG_ECUDA.
+template <int G, int V, int U, int P, bool ST = false>
 __device__ __forceinline__ void finish_query(const SearchArgs &a, WarpSmem &s, const SearchOut &o, int64_t qi,
-                                             int kq, const float *qp, bool rerank) {
+                                             int kq, const float *qp, bool rerank, const StageRef *sr = nullptr) {
     const unsigned lane = lane_id();
     const uint64_t *res = s.pool;
     int rsize = o.size;
@@ -151,16 +170,27 @@ __device__ __forceinline__ void finish_query(const SearchArgs &a, WarpSmem &s, c
         uint64_t *cl = a.C > 0 ? s.clist : reinterpret_cast<uint64_t *>(s.hash);
         // the re-rank gathers all L pool rows at once: more rows in flight
         // than the traversal for rows of 513..1024 values
-        constexpr int UR = V == 8 ? NSG_U_RERANK_WIDE : U;
+        // (staged kernels: the ring serves the re-rank; the register gather is
+        // only the fallback for a ring too small for one FP32 row)
+        constexpr int UR = ST ? 1 : (V == 8 ? NSG_U_RERANK_WIDE : U);
         DistF32<G, V, UR> exact{{}, a.base4, a.dp4};
         exact.Q.load(qp, a.d, a.dp4);
         int kept = 0;
-        for (int c0 = 0; c0 < o.size; c0 += a.W) {
-            const int mm = o.size - c0 < a.W ? o.size - c0 : a.W;
-            for (int t = lane; t < mm; t += 32) s.ids[t] = kid(s.pool[c0 + t]);
-            __syncwarp();
-            exact(s.ids, mm, s.keys);
-            warp_merge(cl, kq, kept, s.keys, mm, s.ck, s.cp, s.sk, s.sp);
+        auto rerank_with = [&](const auto &dist) {
+            for (int c0 = 0; c0 < o.size; c0 += a.W) {
+                const int mm = o.size - c0 < a.W ? o.size - c0 : a.W;
+                for (int t = lane; t < mm; t += 32) s.ids[t] = kid(s.pool[c0 + t]);
+                __syncwarp();
+                dist(s.ids, mm, s.keys);
+                warp_merge(cl, kq, kept, s.keys, mm, s.ck, s.cp, s.sk, s.sp);
+            }
+        };
+        if constexpr (ST) {
+            const int nb = stage_slots(exact, *sr);
+            if (nb > 0) rerank_with(DistStaged<DistF32<G, V, UR>>{exact, *sr, nb, exact.row_bytes()});
+            else rerank_with(exact);
+        } else {
+            rerank_with(exact);
         }
         res = cl;
         rsize = kept;
@@ -174,7 +204,9 @@ __device__ __forceinline__ void finish_query(const SearchArgs &a, WarpSmem &s, c
     if (lane == 0) {
         if (a.n_expand) a.n_expand[qi] = o.n_expand;
         if (a.n_dist) a.n_dist[qi] = o.n_dist;
-        if (a.status) a.status[qi] = o.capped ? -4 : 0;
+        bool failed = false;
+        if constexpr (ST) failed = sr->state[1] != 0;
+        if (a.status) a.status[qi] = failed ? -3 : o.capped ? -4 : 0;
         if (o.capped && a.any_capped) atomicOr(a.any_capped, 1);
     }
     __syncwarp();
@@ -183,7 +215,7 @@ __device__ __forceinline__ void finish_query(const SearchArgs &a, WarpSmem &s, c
 // Alg. 1 per query, one warp each.  P = PREC_F32: distances on the FP32 rows
 // (the plain form).  P = PREC_BF16 / PREC_FP8 / PREC_U8: traversal distances
 // on the low-precision copy, then the FP32 re-rank when asked for.
-template <int G, int V, int U, int P, bool STOP, bool GP>
+template <int G, int V, int U, int P, bool STOP, bool GP, bool ST = false>
 __device__ __forceinline__ void search_body(const SearchArgs &a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -192,6 +224,10 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
     const size_t wbytes = warp_smem_bytes(Ls, a.W, a.C, a.H, true);
     WarpSmem s = carve_warp_smem(smem + warp * wbytes, Ls, a.W, a.C, a.H, true);
     if constexpr (GP) s.pool = a.gpool + ((int64_t)blockIdx.x * wpb + warp) * a.L;
+    StageRef sref{};
+    if constexpr (ST)  // the rings follow the warps' regions (no stop model here)
+        sref = stage_init(smem + wpb * wbytes + warp * stage_bytes(a.stage_nb, a.stage_rb), a.stage_nb, a.stage_rb,
+                          a.any_capped);
     // the stop model lives after the warps' regions, widened to FP32
     StopMLP *mlp = reinterpret_cast<StopMLP *>(smem + wpb * wbytes);
     if (STOP && a.stop_model != nullptr) {
@@ -227,13 +263,13 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
         const InitRand ir{a.init_count < Lq ? a.init_count : Lq, a.init_seed, qi, a.n};
         const InitRand *initp = a.init_count > 0 ? &ir : nullptr;
         SearchOut o;
-        const bool qexact = with_dist<G, V, U, P>(a, qp, [&](const auto &dist) {
+        const bool qexact = with_dist<G, V, U, P, ST>(a, qp, &sref, [&](const auto &dist) {
             o = warp_alg1<false, false, std::decay_t<decltype(dist)>, STOP>(
                 dist, GraphRef{a.adj, a.width}, start, Lq, s, (uint32_t)a.H - 1, a.hshift, a.max_steps, -1, 0,
                 csize, nullptr, 0, scp, nullptr, initp);
         });
         const bool rerank = a.rerank == 1 || (P == PREC_U8 && a.rerank == 2 && !qexact);
-        finish_query<G, V, U, P>(a, s, o, qi, kq, qp, rerank);
+        finish_query<G, V, U, P, ST>(a, s, o, qi, kq, qp, rerank, &sref);
     }
 }
 
@@ -245,7 +281,7 @@ struct GroupCtl {
     int m, done;
 };
 
-template <int G, int V, int U, int P, int WPQ, bool GP>
+template <int G, int V, int U, int P, int WPQ, bool GP, bool ST = false>
 __device__ __forceinline__ void search_group_body(const SearchArgs &a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -256,6 +292,12 @@ __device__ __forceinline__ void search_group_body(const SearchArgs &a) {
     WarpSmem s = carve_warp_smem(smem + g * wbytes, Ls, a.W, a.C, a.H, true);
     if constexpr (GP) s.pool = a.gpool + ((int64_t)blockIdx.x * gpb + g) * a.L;
     volatile GroupCtl *ctl = reinterpret_cast<volatile GroupCtl *>(smem + gpb * wbytes) + g;
+    StageRef sref{};
+    if constexpr (ST) {  // one ring per warp, after the groups' regions and control words
+        const size_t off = (gpb * wbytes + gpb * sizeof(GroupCtl) + 15) & ~size_t(15);
+        sref = stage_init(smem + off + warp * stage_bytes(a.stage_nb, a.stage_rb), a.stage_nb, a.stage_rb,
+                          a.any_capped);
+    }
     const int bar_id = 1 + g;
     const int64_t stride = (int64_t)gridDim.x * gpb;
     int64_t tstat = (int64_t)blockIdx.x * gpb + g;
@@ -273,12 +315,12 @@ __device__ __forceinline__ void search_group_body(const SearchArgs &a) {
         const InitRand ir{a.init_count < Lq ? a.init_count : Lq, a.init_seed, qi, a.n};
         const InitRand *initp = a.init_count > 0 ? &ir : nullptr;
         SearchOut o;
-        const bool qexact = with_dist<G, V, U, P>(a, qp, [&](const auto &dist) {
+        const bool qexact = with_dist<G, V, U, P, ST>(a, qp, &sref, [&](const auto &dist) {
             o = group_alg1<WPQ>(dist, GraphRef{a.adj, a.width}, start, Lq, s, (uint32_t)a.H - 1, a.hshift,
                                 a.max_steps, w, bar_id, ctl, initp);
         });
         const bool rerank = a.rerank == 1 || (P == PREC_U8 && a.rerank == 2 && !qexact);
-        if (w == 0) finish_query<G, V, U, P>(a, s, o, qi, kq, qp, rerank);
+        if (w == 0) finish_query<G, V, U, P, ST>(a, s, o, qi, kq, qp, rerank, &sref);
     }
 }
 
@@ -313,6 +355,15 @@ template <int G, int V, int U, int P, int WPQ, bool GP>
 __global__ void __launch_bounds__(256) search_group_wide_kernel(SearchArgs a) {
     search_group_body<G, V, U, P, WPQ, GP>(a);
 }
+// Staged row gathers (rows of more than 512 values; stage.cuh).
+template <int G, int V, int U, int P, bool GP>
+__global__ void __launch_bounds__(256) search_staged_kernel(SearchArgs a) {
+    search_body<G, V, U, P, false, GP, true>(a);
+}
+template <int G, int V, int U, int P, int WPQ, bool GP>
+__global__ void __launch_bounds__(256) search_group_staged_kernel(SearchArgs a) {
+    search_group_body<G, V, U, P, WPQ, GP, true>(a);
+}
 
 // Kernel for precision P at the dispatch shape G, V, U (wpq warps per query;
 // the learned-stop / trace kernels run one warp per query), pools in shared
@@ -330,6 +381,13 @@ static void (*search_entry(bool stop, int wpq))(SearchArgs) {
         if (wpq == 4) return search_group_wide_kernel<G, V, U, P, 4, GP>;
         return search_wide_kernel<G, V, U, P, GP>;
     }
+}
+
+template <int G, int V, int U, int P, bool GP>
+static void (*staged_entry(int wpq))(SearchArgs) {
+    if (wpq == 2) return search_group_staged_kernel<G, V, U, P, 2, GP>;
+    if (wpq == 4) return search_group_staged_kernel<G, V, U, P, 4, GP>;
+    return search_staged_kernel<G, V, U, P, GP>;
 }
 
 template <typename K>
@@ -357,16 +415,28 @@ static cudaError_t config(K kernel, size_t smem_per_warp, int want_wpb, int64_t 
 
 // Launch of the search kernels for the launch description `a`: pools in
 // shared memory (GP false) or in the global slots a.gpool (GP true, at most
-// gpool_slots resident warps or groups).
-template <bool GP>
+// gpool_slots resident warps or groups); ST: the staged-gather kernels (rows
+// of more than 512 values, no stop model).
+template <bool GP, bool ST = false>
 cudaError_t launch_search_args(const SearchArgs &a, const SearchLaunch &l, size_t per_warp, size_t per_cta,
                                bool stop, int wpq, cudaStream_t st) {
     cudaError_t err = cudaSuccess;
     NSG_DISPATCH_DP4(a.dp4, {
-        auto kern = l.precision == PREC_BF16  ? search_entry<G_, V_, U_, PREC_BF16, GP>(stop, wpq)
-                    : l.precision == PREC_FP8 ? search_entry<G_, V_, U_, PREC_FP8, GP>(stop, wpq)
-                    : l.precision == PREC_U8  ? search_entry<G_, V_, U_, PREC_U8, GP>(stop, wpq)
-                                              : search_entry<G_, V_, U_, PREC_F32, GP>(stop, wpq);
+        void (*kern)(SearchArgs) = nullptr;
+        if constexpr (ST) {
+            if constexpr (V_ >= 8)
+                if (!stop)
+                    kern = l.precision == PREC_BF16  ? staged_entry<G_, V_, U_, PREC_BF16, GP>(wpq)
+                           : l.precision == PREC_FP8 ? staged_entry<G_, V_, U_, PREC_FP8, GP>(wpq)
+                           : l.precision == PREC_U8  ? staged_entry<G_, V_, U_, PREC_U8, GP>(wpq)
+                                                     : staged_entry<G_, V_, U_, PREC_F32, GP>(wpq);
+        } else {
+            kern = l.precision == PREC_BF16  ? search_entry<G_, V_, U_, PREC_BF16, GP>(stop, wpq)
+                   : l.precision == PREC_FP8 ? search_entry<G_, V_, U_, PREC_FP8, GP>(stop, wpq)
+                   : l.precision == PREC_U8  ? search_entry<G_, V_, U_, PREC_U8, GP>(stop, wpq)
+                                             : search_entry<G_, V_, U_, PREC_F32, GP>(stop, wpq);
+        }
+        if (kern == nullptr) return cudaErrorInvalidValue;
         int grid, wpb;
         size_t smem;
         err = config(kern, per_warp, l.warps_per_cta, l.nq * wpq, &grid, &wpb, &smem, per_cta, wpq);
@@ -384,9 +454,14 @@ cudaError_t launch_search_args(const SearchArgs &a, const SearchLaunch &l, size_
     return err;
 }
 
-// The global-memory instantiation lives in its own translation unit
-// (search_global.cu) so the two compile in parallel.
+// The global-memory and staged instantiations live in translation units of
+// their own (search_global.cu, search_staged.cu, search_staged_global.cu) so
+// they compile in parallel.
 cudaError_t launch_search_global(const SearchArgs &a, const SearchLaunch &l, size_t per_warp, size_t per_cta,
                                  bool stop, int wpq, cudaStream_t st);
+cudaError_t launch_search_staged(const SearchArgs &a, const SearchLaunch &l, size_t per_warp, int wpq,
+                                 cudaStream_t st);
+cudaError_t launch_search_staged_global(const SearchArgs &a, const SearchLaunch &l, size_t per_warp, int wpq,
+                                        cudaStream_t st);
 
 }  // namespace nsg

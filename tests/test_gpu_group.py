@@ -49,7 +49,8 @@ def test_group_search_equals_oracle(nsg, tiny, wpq, prec, wpc):
 def test_group_random_init_and_default_hash(nsg, tiny, wpq):
     base, q, ref = tiny
     idx = nsg.nsg_index_from_graph(T(base), T(ref["adj"]), ref["nav"], deg=T(ref["deg"]))
-    one = idx.search_ex(T(q), 10, 60, params=nsg.SearchParams(0, 0, 0, 0, -1, None, 0.5, 0, 0, 25, 3))
+    one = idx.search_ex(T(q), 10, 60, params=nsg.SearchParams(0, 0, 0, 0, -1, None, 0.5, 0, 0, 25, 3,
+                                                              warps_per_query=1))
     grp = idx.search_ex(T(q), 10, 60, params=nsg.SearchParams(0, 0, 0, 0, -1, None, 0.5, 0, 0, 25, 3,
                                                               warps_per_query=wpq))
     assert torch.equal(one["ids"], grp["ids"]) and torch.equal(one["d2"], grp["d2"])
@@ -74,8 +75,10 @@ def test_group_batched_and_validation(nsg, tiny):
     base, q, ref = tiny
     idx = nsg.nsg_index_from_graph(T(base), T(ref["adj"]), ref["nav"], deg=T(ref["deg"]))
     k, L = datagen.uneven_k_L(len(q), seed=9, ks=(1, 10, 50), l_lo=20, l_hi=150)
-    one = idx.search_batched(T(q), T(k), T(L))
+    one = idx.search_batched(T(q), T(k), T(L), params=nsg.SearchParams(warps_per_query=1))
     grp = idx.search_batched(T(q), T(k), T(L), params=nsg.SearchParams(warps_per_query=4))
+    auto = idx.search_batched(T(q), T(k), T(L))  # warps per query left to the library
+    assert torch.equal(one["ids"], auto["ids"]) and torch.equal(one["d2"], auto["d2"])
     assert torch.equal(one["ids"], grp["ids"]) and torch.equal(one["d2"], grp["d2"])
     with pytest.raises(nsg.NsgError):
         idx.search_ex(T(q), 10, 60, params=nsg.SearchParams(warps_per_query=3))
