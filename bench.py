@@ -25,6 +25,12 @@ resident in HBM.  The base (512 MB) is larger than L2 (129 MB).
 on page-locked host memory: host->device copy of the queries, search,
 device->host copy of the ids, all inside the call.
 
+`configs` (the default SIFT-shaped run at N = 1): the GIST-shaped precision
+configuration (1M x 960 float, 1,000 queries: plain, BF16, FP8, U8 forms) and
+the DEEP-shaped batched one (10M x 96 unit vectors, 100,000 uneven queries in
+one autotuned, graph-replayed launch), each a `--compact` run of this script
+in a child process (its own short L grid, no learned stop), summarised.
+
 Multi-GPU: queries are independent, so each rank searches its own batch on
 its own replica of the index (weak scaling, no collective on the data path).
 
@@ -68,9 +74,11 @@ WORKLOADS = {
                  desc="sift-shaped 1,000,000 x 128 int 0..255 GMM(100), 10,000 queries", integer=True),
     "gist": dict(build=dict(K=100, L=60, R=70, C=500),
                  L_grid=[10, 20, 40, 60, 80, 100, 150, 200, 300, 400, 500, 1000, 2000, 4000],
+                 compact_grid=[100, 200, 300, 400, 600, 1000, 2000], compact_forms=("bf16", "fp8", "u8"),
                  k=100, desc="gist-shaped 1,000,000 x 960 f32 [0,1] GMM(50), 1,000 queries"),
     "deep": dict(build=dict(K=64, L=60, R=32, C=500),
                  L_grid=[20, 40, 60, 100, 150, 200, 300, 400, 500, 700, 1000, 2000, 4000],
+                 compact_grid=[200, 400, 700, 1000], compact_forms=("u8",),
                  k=100, desc="deep-shaped 10,000,000 x 96 f32 unit-norm GMM(1000), 100,000 queries"),
     # the paper's own synthetic sets (Table 1); R = 220 is the maximum out-degree it reports for them
     "rand4m": dict(build=dict(K=100, L=60, R=220, C=500),
@@ -97,6 +105,10 @@ def parse():
     p.add_argument("--naive", action="store_true", help="also build and sweep NSG-Naive (ablation)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the partition-and-merge and nn-descent legs")
+    p.add_argument("--compact", action="store_true",
+                   help="the workload's own forms on a short L grid, no learned stop (a configuration run)")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the GIST- and DEEP-shaped configuration runs the default SIFT-shaped line carries")
     p.add_argument("--profile-case", choices=["search", "knn", "build", "nndescent", "partitioned"], default=None,
                    help="run one kernel family on a small SIFT-shaped case for a profiler")
     p.add_argument("--n", type=int, default=300000, help="--profile-case: base rows")
@@ -548,6 +560,42 @@ def ground_truth(capi, bt, qt, W, k=10):
             os.environ["NSG_KNN_ENGINE"] = old
 
 
+# The configurations the default SIFT-shaped line carries besides its own: the
+# GIST-shaped precision forms (1M x 960, 1,000 queries) and the DEEP-shaped
+# batched uneven queries (10M x 96, 100,000 queries), each a compact run of
+# this script in a child process, with a time limit in seconds.
+CONFIG_RUNS = (("gist", 360), ("deep", 480))
+CONFIG_KEYS = ("metric", "value", "unit", "ms_per_step", "dtype", "config", "operating_point", "plain",
+               "chosen_over_plain", "roofline", "e2e", "clocks", "gpu_launches", "build_seconds", "batched",
+               "precision_error_vs_fp64")
+
+
+def config_runs(args):
+    out = {}
+    for wl, limit in CONFIG_RUNS:
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", wl, "--compact", "--no-extras", "--no-cpu",
+               "--steps", str(args.steps), "--warmup", str(args.warmup)]
+        t0 = time.perf_counter()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=limit)
+        except subprocess.TimeoutExpired:
+            out[wl] = {"error": "no result within %d s" % limit}
+            continue
+        lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+        if r.returncode != 0 or not lines:
+            tail = (r.stderr.strip().splitlines() or ["?"])[-1]
+            out[wl] = {"error": "exit %d: %s" % (r.returncode, tail[:300])}
+            continue
+        d = json.loads(lines[-1])
+        res = {k: d.get(k) for k in CONFIG_KEYS}
+        res["at_recall10"] = {t: {f: ({"L": v["L"], "qps": v["qps"]} if v else None)
+                                  for f, v in d["at_recall10"][t]["best"].items()} for t in d.get("at_recall10", {})}
+        res["command"] = " ".join(["python", "bench.py"] + cmd[2:])
+        res["seconds"] = time.perf_counter() - t0
+        out[wl] = res
+    return out
+
+
 def main():
     args = parse()
     if args.profile_case:
@@ -577,6 +625,8 @@ def main():
     # inputs: same base on every rank (a replica), a distinct query batch per rank
     W = WORKLOADS[args.workload]
     BUILD, L_GRID, K_RESULTS = W["build"], W["L_grid"], W["k"]
+    if args.compact:
+        L_GRID = W.get("compact_grid", L_GRID)
     base, q = datagen.workload(args.workload, seed_query=rank_query_seed(rank, datagen.SEED_QUERY))
     n, d = base.shape
     nq = len(q)
@@ -593,27 +643,31 @@ def main():
     # traversal with FP32 accumulation; FP32 re-rank of the pool when the copy is lossy)
     forms = {"plain": capi.SearchParams(0, 0, capi.PREC_F32, 0)}
     for name, prec in (("bf16", capi.PREC_BF16), ("fp8", capi.PREC_FP8), ("u8", capi.PREC_U8)):
+        if args.compact and name not in W.get("compact_forms", (name,)):
+            continue
         idx.prepare(prec)
         forms[name] = capi.SearchParams(0, 0, prec, 0, -1)
-    # learned early termination: traces of a separate query batch (its own
-    # seed, never timed) -> MLP trained on the GPU -> stop rule in the kernel
-    _, q_train = datagen.workload(args.workload, nq=nq, seed_query=datagen.SEED_QUERY + 500 + 1000 * rank)
-    t1 = time.perf_counter()
-    # traces at three pool sizes (the features are relative to L), one model
-    qtr = torch.from_numpy(q_train).cuda()
-    parts = [idx.search_trace(qtr[i::len(STOP_TRACE_LS)].contiguous(), 10, Lt, STOP_TRACE_CAP,
-                              params=capi.SearchParams(0, 0, capi.PREC_F32, 0, -1, None, 0.5, 10))
-             for i, Lt in enumerate(STOP_TRACE_LS)]
-    trace = {key: torch.cat([t[key] for t in parts]) for key in ("feat", "flag", "steps")}
-    del parts
-    stop_model, _, stop_loss = capi.nsg_stop_train(trace, iters=STOP_ITERS, lr=1e-2, seed=1)
-    del trace
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t1
-    for th in STOP_THRESHOLDS:
-        for base_name in ("plain", "u8"):
-            b = forms[base_name]
-            forms[f"{base_name}+stop{th}"] = capi.SearchParams(0, 0, b.precision, 0, -1, stop_model, th, 10)
+    train_s, stop_loss = None, None
+    if not args.compact:
+        # learned early termination: traces of a separate query batch (its own
+        # seed, never timed) -> MLP trained on the GPU -> stop rule in the kernel
+        _, q_train = datagen.workload(args.workload, nq=nq, seed_query=datagen.SEED_QUERY + 500 + 1000 * rank)
+        t1 = time.perf_counter()
+        # traces at three pool sizes (the features are relative to L), one model
+        qtr = torch.from_numpy(q_train).cuda()
+        parts = [idx.search_trace(qtr[i::len(STOP_TRACE_LS)].contiguous(), 10, Lt, STOP_TRACE_CAP,
+                                  params=capi.SearchParams(0, 0, capi.PREC_F32, 0, -1, None, 0.5, 10))
+                 for i, Lt in enumerate(STOP_TRACE_LS)]
+        trace = {key: torch.cat([t[key] for t in parts]) for key in ("feat", "flag", "steps")}
+        del parts
+        stop_model, _, stop_loss = capi.nsg_stop_train(trace, iters=STOP_ITERS, lr=1e-2, seed=1)
+        del trace
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t1
+        for th in STOP_THRESHOLDS:
+            for base_name in ("plain", "u8"):
+                b = forms[base_name]
+                forms[f"{base_name}+stop{th}"] = capi.SearchParams(0, 0, b.precision, 0, -1, stop_model, th, 10)
     info = idx.info()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     outs = {}  # output buffers per result size
@@ -679,6 +733,8 @@ def main():
     prec_err = {}
     qs_n = min(200, nq)
     for name, scale in (("bf16", 1.0), ("fp8", info["fp8_scale"]), ("u8", info["u8_scale"])):
+        if name not in forms:
+            continue
         o = idx.search_ex(qt[:qs_n], 10, L_GRID[len(L_GRID) // 2],
                           params=capi.SearchParams(0, 0, forms[name].precision, 0, 0), counters=False)
         ids_s = o["ids"].cpu().numpy()
@@ -894,13 +950,15 @@ def main():
             "partitioned": extras.get("partitioned"),
             "nndescent": extras.get("nndescent"),
             "nsg_naive": naive,
-            "learned_stop": {"train_queries": nq, "trace_L": list(STOP_TRACE_LS), "iters": STOP_ITERS,
-                             "train_seconds": train_s, "loss_first": stop_loss[0].item(),
-                             "loss_last": stop_loss[-1].item(), "thresholds": STOP_THRESHOLDS},
+            "learned_stop": None if stop_loss is None else {
+                "train_queries": nq, "trace_L": list(STOP_TRACE_LS), "iters": STOP_ITERS, "train_seconds": train_s,
+                "loss_first": stop_loss[0].item(), "loss_last": stop_loss[-1].item(), "thresholds": STOP_THRESHOLDS},
             "precision_error_vs_fp64": prec_err,
             "at_recall10": at_recall,
             "sweep": sweeps,
         }
+        if args.workload == "sift" and world == 1 and not (args.no_configs or args.compact):
+            line["configs"] = config_runs(args)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
