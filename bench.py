@@ -116,7 +116,7 @@ def parse():
     p.add_argument("--L", type=int, default=150, help="--profile-case search: pool size")
     p.add_argument("--K", type=int, default=100, help="--profile-case knn: neighbours per row")
     p.add_argument("--prec", type=int, default=0, help="--profile-case search: 0 FP32, 1 BF16, 2 FP8, 3 U8")
-    p.add_argument("--wpq", type=int, default=1, help="--profile-case search: warps per query")
+    p.add_argument("--wpq", type=int, default=1, help="--profile-case search: warps per query (0: the library's)")
     p.add_argument("--reps", type=int, default=2, help="--profile-case search: launches")
     return p.parse_args()
 
@@ -208,7 +208,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sm)}
 
 
-SEARCH_SOURCES = ("common.cuh", "search_core.cuh", "lowp.cuh", "search_kern.cuh", "search.cu")
+SEARCH_SOURCES = ("common.cuh", "search_core.cuh", "lowp.cuh", "stage.cuh", "search_kern.cuh", "search.cu")
 PRUNE_SOURCES = ("common.cuh", "search_core.cuh", "build.cu")
 
 
@@ -252,17 +252,17 @@ def kernel_source_hash(files=SEARCH_SOURCES):
 # profiles/search_kernel_u8_sift.md has the capture.  A source change changes
 # the hash, and `traffic` is null until re-measured.
 NCU_TRAFFIC = {
-    ("95c42f7aed64dad1", "sift", "u8", 138): (1_515_921_664 + 16_310_272) / 10_000,
+    ("db5b0a1cdd2144ce", "sift", "u8", 138): (1_516_118_528 + 16_316_928) / 10_000,
 }
 # warp instructions of one search launch, per query (smsp__inst_executed.sum of the
 # same capture command with that metric), keyed like NCU_TRAFFIC: the issue roofline
 NCU_INSTRUCTIONS = {
-    ("95c42f7aed64dad1", "sift", "u8", 138): 1_369_312_578 / 10_000,
+    ("db5b0a1cdd2144ce", "sift", "u8", 138): 1_369_312_578 / 10_000,
 }
 # the same for the MRNG edge selection of the build, per node, keyed by
 # (source hash, workload): profiles/prune_kernel_sift1m.md
 PRUNE_TRAFFIC = {
-    ("ac51e03d3f24d394", "sift"): (18_539_054_336 + 134_604_800 + 16_068_004_352 + 113_740_800) / 1_000_000,
+    ("4744460958126e69", "sift"): (18_545_727_232 + 135_220_736 + 16_066_647_040 + 114_126_592) / 1_000_000,
 }
 
 
@@ -319,8 +319,9 @@ def cpu_alg1(adj, deg, base, nav, q, k, L, budget_s=8.0):
 
 
 def profile_case(args):
-    """One kernel family on a small SIFT-shaped case, for a profiler: `search`
-    builds an index (K=100, L=40, R=50, C=500) on an n-row base and runs
+    """One kernel family on a small case of --workload (SIFT-shaped by
+    default), for a profiler: `search` builds an index (the workload's build
+    parameters; SIFT-shaped K=100, L=40, R=50, C=500) on an n-row base and runs
     `--reps` searches of nq queries (top 100, pool --L) in the precision form
     --prec with --wpq warps per query; `knn` runs one brute-force kNN graph
     (K = --K); `build` one index construction; `nndescent` one nn-descent
@@ -334,8 +335,9 @@ def profile_case(args):
 
     nsg_build_mod.build()
     torch.cuda.set_device(0)
-    base, q = datagen.workload("sift", n=args.n, nq=args.nq)
+    base, q = datagen.workload(args.workload, n=args.n, nq=args.nq)
     bt, qt = torch.from_numpy(base).cuda(), torch.from_numpy(q).cuda()
+    B = WORKLOADS[args.workload]["build"]
     if args.profile_case == "knn":
         capi.nsg_knn_init(bt, args.K, with_d2=False)
         torch.cuda.synchronize()
@@ -356,7 +358,7 @@ def profile_case(args):
         torch.cuda.synchronize()
         print(f"partitioned n={args.n} nq={args.nq} L={args.L} prec={args.prec} done")
         return
-    idx = capi.nsg_build(bt, 100, 40, 50, 500)
+    idx = capi.nsg_build(bt, B["K"], B["L"], B["R"], B["C"])
     if args.profile_case == "build":
         torch.cuda.synchronize()
         print(f"build n={args.n} done: {idx.info()}")
