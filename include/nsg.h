@@ -92,7 +92,10 @@ typedef struct {
                               rows in flight per warp), 1..NSG_STAGE_MAX staged: each warp
                               copies up to that many rows at once into a ring of shared-memory
                               slots with the bulk-copy (TMA) engine and measures them there
-                              (fewer where one query's warps would not fit in a block).
+                              (fewer where one query's warps would not fit in a block; the
+                              BF16 / FP8 / U8 copies of rows of at most 2 KB four rows per
+                              copy, a tile::gather4 through a tensor map that
+                              nsg_index_prepare encodes).
                               Auto stages traversal rows of more than 2 KB (FP32 rows of more
                               than 512 values) with 4 slots: bulk copies of rows picked at
                               random complete about one after another, so staging beats the

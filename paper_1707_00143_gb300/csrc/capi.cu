@@ -38,6 +38,7 @@ struct nsg_index {
     float lowp_scale[4] = {1, 1, 1, 1};     // query multiplier
     float lowp_lo[4] = {0, 0, 0, 0};        // U8 offset
     int lowp_exact[4] = {0, 0, 0, 0};       // every value (U8: every distance) survived
+    void *lowp_map[4] = {nullptr, nullptr, nullptr, nullptr};  // device tensor maps for staged four-row gathers
     int max_degree = 0;
     double avg_degree = 0.0;
     int64_t n_fixup = 0;
@@ -447,6 +448,8 @@ void destroy(nsg_index *ix) {
     if (ix->flag) cudaFree(ix->flag);
     if (ix->work) cudaFree(ix->work);
     for (void *p : ix->lowp)
+        if (p) cudaFree(p);
+    for (void *p : ix->lowp_map)
         if (p) cudaFree(p);
     if (ix->host_q) cudaFree(ix->host_q);
     if (ix->host_ids) cudaFree(ix->host_ids);
@@ -1021,6 +1024,7 @@ nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t n
     if (p.precision != NSG_PREC_F32) {
         l.precision = p.precision;
         l.lowp = idx->lowp[p.precision];
+        l.lowp_map = idx->lowp_map[p.precision];
         l.lowp_chunks = idx->lowp_dpl[p.precision] * (p.precision == NSG_PREC_BF16 ? 2 : 1) / 16;
         l.lowp_scale = idx->lowp_scale[p.precision];
         l.lowp_lo = idx->lowp_lo[p.precision];
@@ -1488,6 +1492,17 @@ nsg_status nsg_index_prepare(nsg_index *idx, int32_t precision, void *stream) {
     // U8 keys are exact only when the integer sum fits FP32 exactly: d * 255^2 < 2^24
     idx->lowp_exact[precision] =
         !inexact && (precision != NSG_PREC_U8 || (exact_map && (int64_t)idx->d * 65025 < (1 << 24)));
+    // rows of more than 512 values and at most 2 KB: a tensor map for the
+    // staged gathers, four rows per copy (none: one bulk copy per row)
+    const int row_bytes = dpl * (precision == NSG_PREC_BF16 ? 2 : 1);
+    alignas(64) unsigned char map[128];
+    if (idx->dp > 512 && nsg::make_gather_map(map, idx->lowp[precision], idx->n, row_bytes)) {
+        DevBuf<unsigned char> dmap;
+        NSG_CK(dmap.alloc(sizeof(map)));
+        NSG_CK(cudaMemcpyAsync(dmap.p, map, sizeof(map), cudaMemcpyHostToDevice, st));
+        NSG_CK(cudaStreamSynchronize(st));
+        idx->lowp_map[precision] = dmap.release();
+    }
     return NSG_OK;
 }
 

@@ -64,9 +64,12 @@ struct SearchLaunch {
     uint64_t *gpool = nullptr;
     int64_t gpool_slots = 0;
     // staged row gathers for rows of more than 512 values (stage.cuh): 0 off,
-    // > 0 that many slots per warp (at most 32), < 0 chosen by the launch
-    // (search_stage_slots)
+    // > 0 that many rows in flight per warp (at most 32), < 0 chosen by the
+    // launch (search_stage_slots); lowp_map: a device tensor map over the
+    // low-precision rows (make_gather_map) -- they are then gathered four
+    // per copy -- or nullptr
     int stage = 0;
+    const void *lowp_map = nullptr;
 };
 // Approximate kNN graph by nn-descent (nndescent.cu).  base [n][dp] padded
 // rows; ids [n][K] out, d2 [n][K] out (nullable); scratch: at least
@@ -106,8 +109,15 @@ int search_stage_slots(int row_bytes);
 // units (queries, or query-subset pairs) with pools of L keys on rows of `dp`
 // padded values in traversal precision `precision`.
 int search_auto_wpq(int64_t units, int dp, int precision, int L);
-// Slots per warp launch_search gives the staged gathers of `l` (0: none).
+// Rows per warp launch_search gives the staged gathers of `l` (0: none), and
+// the ring they take: slots and bytes per slot.
 int search_stage_resolve(const SearchLaunch &l);
+void stage_layout(const SearchLaunch &l, int nb, int *slots, int *slot_bytes);
+// Encode (host) a 2-D tensor map over `n` rows of `row_bytes` (a multiple of
+// 16, at most 2048) at `rows` for the staged four-row gathers: 8-byte
+// elements, one box = one whole row.  `map` holds 128 bytes.  false: the
+// driver's encoder is unavailable or the rows do not qualify.
+bool make_gather_map(void *map, const void *rows, int64_t n, int row_bytes);
 size_t search_warp_smem_bytes(int L, int W, int H);
 cudaError_t launch_search(const SearchLaunch &a, cudaStream_t st);
 

@@ -1,5 +1,7 @@
 // lowp.cu -- building the BF16 / FP8-e4m3 / U8 copies of the base used by
 // the precision forms of the search.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -7,6 +9,27 @@
 #include "kernels.h"
 
 namespace nsg {
+
+bool make_gather_map(void *map, const void *rows, int64_t n, int row_bytes) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return false;
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    if (row_bytes <= 0 || row_bytes % 16 || row_bytes > 2048 || n < 1 || n > INT32_MAX) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)(row_bytes / 8), (cuuint64_t)n};
+    cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)(row_bytes / 8), 1};  // one whole row, one row high
+    cuuint32_t estr[2] = {1, 1};
+    return fn(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(rows), dims,
+              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 __global__ void absmax_kernel(const float *__restrict__ x, int64_t count, unsigned *out) {
     float m = 0.0f;

@@ -118,12 +118,13 @@ cudaError_t launch_search(const SearchLaunch &l, cudaStream_t st) {
     // staged row gathers: rows of more than 512 values, without the stop kernels
     a.stage_nb = 0;
     a.stage_rb = 0;
+    a.lmap = nullptr;
     if (l.stage > 0 && (stop || a.dp4 <= 128)) return cudaErrorInvalidValue;
     const int nb = search_stage_resolve(l);
     if (nb > 0) {
-        a.stage_nb = nb;
-        a.stage_rb = (l.precision == PREC_F32 ? a.dp4 : a.dc) * 16;
-        const size_t pw = per_warp + stage_bytes(nb, a.stage_rb);
+        stage_layout(l, nb, &a.stage_nb, &a.stage_rb);
+        if (l.precision != PREC_F32) a.lmap = reinterpret_cast<const CUtensorMap *>(l.lowp_map);
+        const size_t pw = per_warp + stage_bytes(a.stage_nb, a.stage_rb);
         return a.gpool != nullptr ? launch_search_staged_global(a, l, pw, wpq, st)
                                   : launch_search_staged(a, l, pw, wpq, st);
     }
@@ -131,8 +132,21 @@ cudaError_t launch_search(const SearchLaunch &l, cudaStream_t st) {
     return launch_search_args<false>(a, l, per_warp, per_cta, stop, wpq, st);
 }
 
-// Slots per warp of the staged gathers launch_search uses for `l` (0: the
-// register gather).
+// The ring for nb staged rows of `l`: one row per slot, or (a tensor map over
+// the low-precision rows) groups of four rows per slot, 128-byte multiples.
+void stage_layout(const SearchLaunch &l, int nb, int *slots, int *slot_bytes) {
+    const int rb = (l.precision == PREC_F32 ? l.dp / 4 : l.lowp_chunks) * 16;
+    if (l.precision != PREC_F32 && l.lowp_map != nullptr) {
+        *slots = std::max(1, nb / 4);
+        *slot_bytes = stage_group_bytes(rb);
+    } else {
+        *slots = nb;
+        *slot_bytes = rb;
+    }
+}
+
+// Rows per warp the staged gathers of `l` hold in flight (0: the register
+// gather).
 int search_stage_resolve(const SearchLaunch &l) {
     const bool stop = l.stop_model != nullptr || l.trace_feat != nullptr;
     const int dp4 = l.dp / 4;
@@ -144,8 +158,12 @@ int search_stage_resolve(const SearchLaunch &l) {
     if (wpq > 1) per_warp = ((per_warp + 32) / wpq + 15) & ~size_t(15);
     const int rb = (l.precision == PREC_F32 ? dp4 : l.lowp_chunks) * 16;
     int nb = l.stage > 0 ? std::min(l.stage, STAGE_MAX_SLOTS) : search_stage_slots(rb);
-    // a block holds at least one query's warps: fewer slots where those would not fit
-    while (nb > 1 && (size_t)wpq * (per_warp + stage_bytes(nb, rb)) > smem_optin()) --nb;
+    // a block holds at least one query's warps: fewer rows where those would not fit
+    for (; nb > 1; --nb) {
+        int slots, sb;
+        stage_layout(l, nb, &slots, &sb);
+        if ((size_t)wpq * (per_warp + stage_bytes(slots, sb)) <= smem_optin()) break;
+    }
     return nb;
 }
 

@@ -91,8 +91,11 @@ struct SearchArgs {
     // global-memory pools: slot (block, warp or group) of L keys, or nullptr
     uint64_t *gpool;
     // staged row gathers (stage.cuh): slots per warp and bytes per slot of
-    // each warp's ring, which follows the warps' (groups') regions
+    // each warp's ring, which follows the warps' (groups') regions; a tensor
+    // map over the low-precision rows gathers them four per copy (nullptr:
+    // one bulk copy per row)
     int stage_nb, stage_rb;
+    const CUtensorMap *lmap;
 };
 
 // Query row and start node of search unit t.
@@ -110,9 +113,9 @@ __device__ __forceinline__ int64_t unit_query(const SearchArgs &a, int64_t t, in
 // share of the query), handed to f.  Returns whether the 8-bit map kept
 // every query value (always true for the other forms).
 template <bool ST, class D, class F>
-__device__ __forceinline__ void run_dist(const D &dist, const StageRef *sr, F &&f) {
+__device__ __forceinline__ void run_dist(const D &dist, const StageRef *sr, const CUtensorMap *map, F &&f) {
     if constexpr (ST) {
-        const DistStaged<D> sd{dist, *sr, stage_slots(dist, *sr), dist.row_bytes()};
+        const DistStaged<D> sd{dist, *sr, stage_slots(dist, *sr, map != nullptr), dist.row_bytes(), map};
         f(sd);
     } else {
         f(dist);
@@ -126,7 +129,7 @@ __device__ __forceinline__ bool with_dist(const SearchArgs &a, const float *qp, 
     if constexpr (P == PREC_F32) {
         DistF32<G, V, U> dist{{}, a.base4, a.dp4};
         dist.Q.load(qp, a.d, a.dp4);
-        run_dist<ST>(dist, sr, f);
+        run_dist<ST>(dist, sr, nullptr, f);
         return true;
     } else if constexpr (P == PREC_U8) {
         // an 8-bit row is a quarter of the FP32 row: G8 lanes of up to
@@ -139,7 +142,7 @@ __device__ __forceinline__ bool with_dist(const SearchArgs &a, const float *qp, 
         constexpr int U8R = V == 8 ? NSG_U8ROWS_WIDE : (V > 8 ? 2 : NSG_U8ROWS);
         DistU8<G8, VC, U8R> dist{{}, a.lowp, a.dc};
         const bool qexact = dist.Q.load(qp, a.d, a.lo, a.scale);
-        run_dist<ST>(dist, sr, f);
+        run_dist<ST>(dist, sr, a.lmap, f);
         return qexact;
     } else {
         constexpr int VC = (V * 4) / PrecEpc<P>::value > 0 ? (V * 4) / PrecEpc<P>::value : 1;
@@ -147,7 +150,7 @@ __device__ __forceinline__ bool with_dist(const SearchArgs &a, const float *qp, 
         constexpr int UL = V == 8 ? NSG_UL_WIDE : (VC <= 1 ? NSG_UL1 : (VC == 2 ? NSG_UL2 : 2));
         DistLp<P, G, VC, UL> dist{{}, a.lowp, a.dc};
         dist.Q.load(qp, a.d, a.scale);
-        run_dist<ST>(dist, sr, f);
+        run_dist<ST>(dist, sr, a.lmap, f);
         return true;
     }
 }
@@ -187,7 +190,7 @@ __device__ __forceinline__ void finish_query(const SearchArgs &a, WarpSmem &s, c
         };
         if constexpr (ST) {
             const int nb = stage_slots(exact, *sr);
-            if (nb > 0) rerank_with(DistStaged<DistF32<G, V, UR>>{exact, *sr, nb, exact.row_bytes()});
+            if (nb > 0) rerank_with(DistStaged<DistF32<G, V, UR>>{exact, *sr, nb, exact.row_bytes(), nullptr});
             else rerank_with(exact);
         } else {
             rerank_with(exact);
@@ -226,8 +229,8 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
     if constexpr (GP) s.pool = a.gpool + ((int64_t)blockIdx.x * wpb + warp) * a.L;
     StageRef sref{};
     if constexpr (ST)  // the rings follow the warps' regions (no stop model here)
-        sref = stage_init(smem + wpb * wbytes + warp * stage_bytes(a.stage_nb, a.stage_rb), a.stage_nb, a.stage_rb,
-                          a.any_capped);
+        sref = stage_init(smem + wpb * wbytes + warp * stage_bytes(a.stage_nb, a.stage_rb), a.stage_nb,
+                          a.stage_rb, a.any_capped);
     // the stop model lives after the warps' regions, widened to FP32
     StopMLP *mlp = reinterpret_cast<StopMLP *>(smem + wpb * wbytes);
     if (STOP && a.stop_model != nullptr) {
