@@ -76,7 +76,10 @@ WORKLOADS = {
                  L_grid=[10, 20, 40, 60, 80, 100, 150, 200, 300, 400, 500, 1000, 2000, 4000],
                  compact_grid=[100, 200, 300, 400, 600, 1000, 2000], compact_forms=("bf16", "fp8", "u8"),
                  k=100, desc="gist-shaped 1,000,000 x 960 f32 [0,1] GMM(50), 1,000 queries"),
-    "deep": dict(build=dict(K=64, L=60, R=32, C=500),
+    # the kNN stage by nn-descent (16 samples, 16 reverse, 12 iterations), as the
+    # paper builds its million-scale kNN graphs (Section 3.6): on this tight
+    # 1,000-cluster mixture the exact graph links mostly within clusters
+    "deep": dict(build=dict(K=64, L=60, R=32, C=500), knn=(16, 16, 12),
                  L_grid=[20, 40, 60, 100, 150, 200, 300, 400, 500, 700, 1000, 2000, 4000],
                  compact_grid=[200, 400, 700, 1000], compact_forms=("u8",),
                  k=100, desc="deep-shaped 10,000,000 x 96 f32 unit-norm GMM(1000), 100,000 queries"),
@@ -268,8 +271,18 @@ PRUNE_TRAFFIC = {
 
 def bench_config(W, world, base):
     """The workload a line measures: the same dict in both arms."""
-    return {"workload": W["desc"], "build": W["build"], "k": W["k"], "target_recall10": TARGET,
+    knn = "exact (tensor-core scan)" if "knn" not in W else "nn-descent (samples %d, reverse %d, iterations %d)" % W["knn"]
+    return {"workload": W["desc"], "build": W["build"], "knn_stage": knn, "k": W["k"], "target_recall10": TARGET,
             "parallelism": f"replicas{world}", "l2": f"inputs larger than L2 ({base.nbytes >> 20} MB base)"}
+
+
+def build_index(capi, bt, W, seed=0):
+    """Alg. 2 on the workload's kNN stage: exact, or nn-descent where W names one."""
+    B = W["build"]
+    if "knn" in W:
+        return capi.nsg_build_ex(bt, B["K"], B["L"], B["R"], B["C"], seed=seed,
+                                 knn_params=capi.NnDescentParams(*W["knn"], 0.001, 1))
+    return capi.nsg_build(bt, B["K"], B["L"], B["R"], B["C"], seed=seed)
 
 
 def _timed_sample(fn, q, per_q_budget, cap):
@@ -358,7 +371,7 @@ def profile_case(args):
         torch.cuda.synchronize()
         print(f"partitioned n={args.n} nq={args.nq} L={args.L} prec={args.prec} done")
         return
-    idx = capi.nsg_build(bt, B["K"], B["L"], B["R"], B["C"])
+    idx = build_index(capi, bt, WORKLOADS[args.workload])
     if args.profile_case == "build":
         torch.cuda.synchronize()
         print(f"build n={args.n} done: {idx.info()}")
@@ -395,7 +408,7 @@ def run_reference(args):
     # the index (setup, untimed): the library's build, equal to the oracle's own
     nsg_build_mod.build()
     torch.cuda.set_device(local)
-    idx = capi.nsg_build(torch.from_numpy(base).cuda(), B["K"], B["L"], B["R"], B["C"], seed=0)
+    idx = build_index(capi, torch.from_numpy(base).cuda(), W, seed=0)
     adj, deg = (t.cpu().numpy() for t in idx.graph())
     nav = idx.info()["nav"]
     del idx
@@ -637,7 +650,7 @@ def main():
     st = torch.cuda.current_stream()
 
     t0 = time.perf_counter()
-    idx = capi.nsg_build(bt, BUILD["K"], BUILD["L"], BUILD["R"], BUILD["C"], seed=0)
+    idx = build_index(capi, bt, W, seed=0)
     build_s = time.perf_counter() - t0
     gt, gt_d2 = ground_truth(capi, bt, qt, W)
 
