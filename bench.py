@@ -28,8 +28,9 @@ device->host copy of the ids, all inside the call.
 `configs` (the default SIFT-shaped run at N = 1): the GIST-shaped precision
 configuration (1M x 960 float, 1,000 queries: plain, BF16, FP8, U8 forms) and
 the DEEP-shaped batched one (10M x 96 unit vectors, 100,000 uneven queries in
-one autotuned, graph-replayed launch), each a `--compact` run of this script
-in a child process (its own short L grid, no learned stop), summarised.
+one autotuned, graph-replayed launch; the 8-bit form's learned stop trained on
+this index's traces), each a `--compact` run of this script in a child
+process (its own short L grid), summarised.
 
 Multi-GPU: queries are independent, so each rank searches its own batch on
 its own replica of the index (weak scaling, no collective on the data path).
@@ -81,7 +82,7 @@ WORKLOADS = {
     # 1,000-cluster mixture the exact graph links mostly within clusters
     "deep": dict(build=dict(K=64, L=60, R=32, C=500), knn=(16, 16, 12),
                  L_grid=[20, 40, 60, 100, 150, 200, 300, 400, 500, 700, 1000, 2000, 4000],
-                 compact_grid=[200, 400, 700, 1000], compact_forms=("u8",),
+                 compact_grid=[200, 400, 700, 1000], compact_forms=("u8",), compact_stop=("u8",),
                  k=100, desc="deep-shaped 10,000,000 x 96 f32 unit-norm GMM(1000), 100,000 queries"),
     # the paper's own synthetic sets (Table 1); R = 220 is the maximum out-degree it reports for them
     "rand4m": dict(build=dict(K=100, L=60, R=220, C=500),
@@ -109,7 +110,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the partition-and-merge and nn-descent legs")
     p.add_argument("--compact", action="store_true",
-                   help="the workload's own forms on a short L grid, no learned stop (a configuration run)")
+                   help="the workload's own forms on a short L grid, learned stop only where the workload "
+                        "names it (a configuration run)")
     p.add_argument("--no-configs", action="store_true",
                    help="skip the GIST- and DEEP-shaped configuration runs the default SIFT-shaped line carries")
     p.add_argument("--profile-case", choices=["search", "knn", "build", "nndescent", "partitioned"], default=None,
@@ -581,8 +583,8 @@ def ground_truth(capi, bt, qt, W, k=10):
 # this script in a child process, with a time limit in seconds.
 CONFIG_RUNS = (("gist", 360), ("deep", 480))
 CONFIG_KEYS = ("metric", "value", "unit", "ms_per_step", "dtype", "config", "operating_point", "plain",
-               "chosen_over_plain", "roofline", "e2e", "clocks", "gpu_launches", "build_seconds", "batched",
-               "precision_error_vs_fp64")
+               "chosen_over_plain", "roofline", "e2e", "clocks", "gpu_launches", "build_seconds", "build_ms", "index",
+               "batched", "precision_error_vs_fp64", "learned_stop")
 
 
 def config_runs(args):
@@ -605,6 +607,7 @@ def config_runs(args):
         res = {k: d.get(k) for k in CONFIG_KEYS}
         res["at_recall10"] = {t: {f: ({"L": v["L"], "qps": v["qps"]} if v else None)
                                   for f, v in d["at_recall10"][t]["best"].items()} for t in d.get("at_recall10", {})}
+        res["stop_vs_fixed_L"] = {t: d["at_recall10"][t].get("stop_vs_fixed_L") for t in d.get("at_recall10", {})}
         res["command"] = " ".join(["python", "bench.py"] + cmd[2:])
         res["seconds"] = time.perf_counter() - t0
         out[wl] = res
@@ -663,10 +666,11 @@ def main():
         idx.prepare(prec)
         forms[name] = capi.SearchParams(0, 0, prec, 0, -1)
     train_s, stop_loss = None, None
-    if not args.compact:
+    stop_bases = W.get("compact_stop", ()) if args.compact else ("plain", "u8")
+    if stop_bases:
         # learned early termination: traces of a separate query batch (its own
         # seed, never timed) -> MLP trained on the GPU -> stop rule in the kernel
-        _, q_train = datagen.workload(args.workload, nq=nq, seed_query=datagen.SEED_QUERY + 500 + 1000 * rank)
+        _, q_train = datagen.workload(args.workload, n=1, nq=nq, seed_query=datagen.SEED_QUERY + 500 + 1000 * rank)
         t1 = time.perf_counter()
         # traces at three pool sizes (the features are relative to L), one model
         qtr = torch.from_numpy(q_train).cuda()
@@ -680,7 +684,7 @@ def main():
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t1
         for th in STOP_THRESHOLDS:
-            for base_name in ("plain", "u8"):
+            for base_name in stop_bases:
                 b = forms[base_name]
                 forms[f"{base_name}+stop{th}"] = capi.SearchParams(0, 0, b.precision, 0, -1, stop_model, th, 10)
     info = idx.info()
