@@ -257,12 +257,12 @@ def kernel_source_hash(files=SEARCH_SOURCES):
 # profiles/search_kernel_u8_sift.md has the capture.  A source change changes
 # the hash, and `traffic` is null until re-measured.
 NCU_TRAFFIC = {
-    ("db5b0a1cdd2144ce", "sift", "u8", 138): (1_516_118_528 + 16_316_928) / 10_000,
+    ("b1e56bdd009c2147", "sift", "u8", 138): (1_516_259_328 + 16_351_488) / 10_000,
 }
 # warp instructions of one search launch, per query (smsp__inst_executed.sum of the
 # same capture command with that metric), keyed like NCU_TRAFFIC: the issue roofline
 NCU_INSTRUCTIONS = {
-    ("db5b0a1cdd2144ce", "sift", "u8", 138): 1_369_312_578 / 10_000,
+    ("b1e56bdd009c2147", "sift", "u8", 138): 1_369_312_578 / 10_000,
 }
 # the same for the MRNG edge selection of the build, per node, keyed by
 # (source hash, workload): profiles/prune_kernel_sift1m.md
