@@ -32,7 +32,10 @@
 #include "search_core.cuh"
 
 // Unreached ids speculated per batch: larger batches run more searches in
-// parallel, smaller ones leave fewer earlier fix-ups to make a speculation stale.
+// parallel, smaller ones leave fewer earlier fix-ups to make a speculation
+// stale.  The batch starts at NSG_CONNECT_BATCH and adapts between
+// CONNECT_MIN_BATCH and CONNECT_MAX_BATCH to the share of speculations the
+// previous batch had to redo (the result does not depend on it).
 #ifndef NSG_CONNECT_U_WIDE8
 #define NSG_CONNECT_U_WIDE8 4  // rows in flight per warp, 513..1024-value rows
 #endif
@@ -43,6 +46,10 @@
 namespace nsg {
 
 namespace {
+
+constexpr int CONNECT_MIN_BATCH = 64;
+constexpr int CONNECT_MAX_BATCH = 1024;
+constexpr int CONNECT_SQ = 2048;  // queue entries of the reach step held in shared memory
 
 __host__ __device__ inline int round32c(int x) { return (x + 31) & ~31; }
 inline int log2c(unsigned x) {
@@ -165,20 +172,45 @@ struct CommitArgs {
     int *out;  // [0] edges added, [1] status, [2] capped, [3] re-searched
 };
 
+// L1 prefetch of fix-up i's speculative pool and expansion log (written by
+// the speculate launch, read-only here), issued one fix-up ahead.
+__device__ __forceinline__ void prefetch_fixup(const CommitArgs &a, int i, int xc, int ps) {
+    const int pool_lines = (ps * 8 + 127) >> 7, x = xc < a.xcap ? xc : 0;
+    const int xlog_lines = (x * 4 + 127) >> 7, xthr_lines = (x * 8 + 127) >> 7;
+    for (int t = threadIdx.x; t < pool_lines + xlog_lines + xthr_lines; t += blockDim.x) {
+        const char *p = t < pool_lines ? reinterpret_cast<const char *>(a.pools + (int64_t)i * a.L) + (t << 7)
+                        : t < pool_lines + xlog_lines
+                            ? reinterpret_cast<const char *>(a.xlog + (int64_t)i * a.xcap) + ((t - pool_lines) << 7)
+                            : reinterpret_cast<const char *>(a.xthr + (int64_t)i * a.xcap) +
+                                  ((t - pool_lines - xlog_lines) << 7);
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+    }
+}
+
 template <int G, int V, int U>
 __global__ void __launch_bounds__(256) commit_kernel(CommitArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int sh_flag, sh_found, sh_size, sh_qtail;
+    __shared__ int s_list[CONNECT_MAX_BATCH], s_xcnt[CONNECT_MAX_BATCH], s_psize[CONNECT_MAX_BATCH];
+    __shared__ int sq[CONNECT_SQ];  // the reach step's queue (entries past it in a.queue)
     const int tid = threadIdx.x, warp = tid >> 5;
     WarpSmem s = carve_warp_smem(smem, a.L, a.W, 0, a.H);
     const int cnt = a.meta[0];
+    for (int t = tid; t < cnt; t += blockDim.x) {
+        s_list[t] = a.list[t];
+        s_xcnt[t] = a.xcnt[t];
+        s_psize[t] = a.psize[t];
+    }
+    __syncthreads();
+    if (cnt > 0) prefetch_fixup(a, 0, s_xcnt[0], s_psize[0]);
     int added = 0, redone = 0, status = 0, capped = 0;
     for (int i = 0; i < cnt; ++i) {
-        const int u = a.list[i];
+        const int u = s_list[i];
+        if (i + 1 < cnt) prefetch_fixup(a, i + 1, s_xcnt[i + 1], s_psize[i + 1]);
         if (bit_is_set(a.reached, u)) continue;  // reached by an earlier fix-up of this batch
         if (tid == 0) sh_flag = 0;
         __syncthreads();
-        const int xc = a.xcnt[i];
+        const int xc = s_xcnt[i];
         if (xc > a.xcap) {
             if (tid == 0) sh_flag = 1;
         } else {
@@ -228,7 +260,7 @@ __global__ void __launch_bounds__(256) commit_kernel(CommitArgs a) {
             if (sh_flag == 2) capped = 1;
         } else {
             pool = a.pools + (int64_t)i * a.L;
-            size = a.psize[i];
+            size = s_psize[i];
         }
         // first pool entry (key order) whose out-degree is below R
         if (tid == 0) sh_found = INT_MAX;
@@ -257,7 +289,7 @@ __global__ void __launch_bounds__(256) commit_kernel(CommitArgs a) {
             a.deg[sel] = dg + 1;
             if (!(atomicOr(a.dirty + (sel >> 5), 1u << (sel & 31)) & (1u << (sel & 31)))) a.deg0[sel] = dg;
             atomicOr(a.reached + (u >> 5), 1u << (u & 31));
-            a.queue[0] = u;
+            sq[0] = u;
             sh_qtail = 1;
         }
         ++added;
@@ -269,11 +301,16 @@ __global__ void __launch_bounds__(256) commit_kernel(CommitArgs a) {
             __syncthreads();
             const int64_t total = (int64_t)(tail - head) * a.R;
             for (int64_t x = tid; x < total; x += blockDim.x) {
-                const int node = ldv(a.queue + head + x / a.R);
+                const int qi = head + (int)(x / a.R);
+                const int node = qi < CONNECT_SQ ? sq[qi] : ldv(a.queue + qi);
                 const int v = ldv(a.adj + (int64_t)node * a.R + x % a.R);
                 if (v < 0) continue;
                 const uint32_t bit = 1u << (v & 31);
-                if (!(atomicOr(a.reached + (v >> 5), bit) & bit)) a.queue[atomicAdd(&sh_qtail, 1)] = v;
+                if (!(atomicOr(a.reached + (v >> 5), bit) & bit)) {
+                    const int at = atomicAdd(&sh_qtail, 1);
+                    if (at < CONNECT_SQ) sq[at] = v;
+                    else a.queue[at] = v;
+                }
             }
             head = tail;
             __syncthreads();
@@ -301,16 +338,19 @@ struct Buf {
 cudaError_t run_connect(const ConnectLaunch &l, int out_host[4], cudaStream_t st) {
     const int64_t n = l.n;
     const int64_t nwords = (n + 31) / 32;
-    const int B = NSG_CONNECT_BATCH;
+    const int BMAX = CONNECT_MAX_BATCH;
+    int B = NSG_CONNECT_BATCH < CONNECT_MIN_BATCH ? CONNECT_MIN_BATCH
+            : NSG_CONNECT_BATCH > BMAX            ? BMAX
+                                                  : NSG_CONNECT_BATCH;
     const int xcap = 4 * l.L + 64;
     Buf<uint32_t> reached, dirty;
     Buf<int> qa, qb, cnt, list, meta, psize, xlog, xcnt, out, deg0;
     Buf<uint64_t> pools, xthr;
     cudaError_t e;
     if ((e = reached.alloc(nwords)) || (e = dirty.alloc(nwords)) || (e = qa.alloc(n)) || (e = qb.alloc(n)) ||
-        (e = cnt.alloc(2)) || (e = list.alloc(B)) || (e = meta.alloc(2)) || (e = psize.alloc(B)) ||
-        (e = xlog.alloc((size_t)B * xcap)) || (e = xcnt.alloc(B)) || (e = out.alloc(4)) ||
-        (e = pools.alloc((size_t)B * l.L)) || (e = xthr.alloc((size_t)B * xcap)) || (e = deg0.alloc(n)))
+        (e = cnt.alloc(2)) || (e = list.alloc(BMAX)) || (e = meta.alloc(2)) || (e = psize.alloc(BMAX)) ||
+        (e = xlog.alloc((size_t)BMAX * xcap)) || (e = xcnt.alloc(BMAX)) || (e = out.alloc(4)) ||
+        (e = pools.alloc((size_t)BMAX * l.L)) || (e = xthr.alloc((size_t)BMAX * xcap)) || (e = deg0.alloc(n)))
         return e;
     if ((e = cudaMemsetAsync(reached.p, 0, nwords * 4, st)) || (e = cudaMemsetAsync(out.p, 0, 16, st))) return e;
     // reach from the navigating node: level-synchronous BFS
@@ -372,6 +412,7 @@ cudaError_t run_connect(const ConnectLaunch &l, int out_host[4], cudaStream_t st
     const size_t per_warp = warp_smem_bytes(l.L, sa.W, 0, sa.H);
     const int wpb = 4;
     int64_t cursor = 0;
+    int prev[4] = {0, 0, 0, 0};
     for (int64_t batch = 0; batch <= n; ++batch) {
         gather_unreached_kernel<<<1, 256, 0, st>>>(reached.p, n, cursor, B, list.p, meta.p);
         if ((e = cudaGetLastError())) return e;
@@ -402,6 +443,17 @@ cudaError_t run_connect(const ConnectLaunch &l, int out_host[4], cudaStream_t st
         if ((e = cudaMemcpyAsync(o, out.p, sizeof(o), cudaMemcpyDeviceToHost, st))) return e;
         if ((e = cudaStreamSynchronize(st))) return e;
         if (o[1]) break;
+        // a speculation redone in the commit costs a whole serial search, a
+        // larger batch saves a share of one parallel search per fix-up: grow the
+        // batch while at most 1 in 100 speculations were redone, in this batch
+        // and overall, shrink it when more than 1 in 50 of this batch's were
+        // (SIFT-shaped 1M: ~1.8 % at 64, which stays; DEEP-shaped 10M and
+        // GAUSS5M: < 0.5 % up to 1,024, connectivity 16.4 -> 8.4 s and
+        // 19.2 -> 5.3 s)
+        const int fixed = o[0] - prev[0], redone = o[3] - prev[3];
+        if (redone * 100 <= fixed && o[3] * 100 <= o[0] && B < BMAX) B *= 2;
+        else if (redone * 50 > fixed && B > CONNECT_MIN_BATCH) B /= 2;
+        for (int t = 0; t < 4; ++t) prev[t] = o[t];
     }
     if ((e = cudaMemcpyAsync(out_host, out.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st))) return e;
     return cudaStreamSynchronize(st);
