@@ -257,12 +257,12 @@ def kernel_source_hash(files=SEARCH_SOURCES):
 # profiles/search_kernel_u8_sift.md has the capture.  A source change changes
 # the hash, and `traffic` is null until re-measured.
 NCU_TRAFFIC = {
-    ("b1e56bdd009c2147", "sift", "u8", 138): (1_516_259_328 + 16_351_488) / 10_000,
+    ("fc53c47ea7d2373f", "sift", "u8", 138): (1_167_627_264 + 15_439_104) / 10_000,
 }
 # warp instructions of one search launch, per query (smsp__inst_executed.sum of the
 # same capture command with that metric), keyed like NCU_TRAFFIC: the issue roofline
 NCU_INSTRUCTIONS = {
-    ("b1e56bdd009c2147", "sift", "u8", 138): 1_369_312_578 / 10_000,
+    ("fc53c47ea7d2373f", "sift", "u8", 138): 1_369_312_578 / 10_000,
 }
 # the same for the MRNG edge selection of the build, per node, keyed by
 # (source hash, workload): profiles/prune_kernel_sift1m.md
@@ -954,7 +954,8 @@ def main():
             "e2e": {"value": job_qps(world, nq, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": nq * d * 4, "d2h_bytes_per_step": nq * kc * 4,
                     "call": "nsg_search_host", "same_ids_as_device_call": e2e_same},
-            "gpu_launches": args.steps,
+            # per step: the visiting order (distance, bucket, scan, scatter) and the search
+            "gpu_launches": 5 * args.steps,
             "clocks": clocks,
             "build_seconds": build_s,
             "build_ms": {k: info[k] for k in ("ms_knn", "ms_centroid_nav", "ms_collect", "ms_prune",

@@ -1067,12 +1067,55 @@ nsg_status ensure_gpool(const nsg_index *idx, nsg::SearchLaunch &l, cudaStream_t
     return host_guard([&] { return ensure_gpool_body(idx, l, st); });
 }
 
+// The library's own stream-ordered pool for per-call scratch on this device:
+// it keeps what it has mapped (release threshold: never), where the default
+// pool gives it back at every synchronisation and the next call maps it
+// again.  Created once per device, kept until the process exits.
+cudaMemPool_t scratch_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = p;
+    }
+    return pools[dev];
+}
+
 nsg_status launch_dynamic(const nsg_index *idx, nsg::SearchLaunch l, cudaStream_t st) {
     if (nsg_status s = ensure_gpool(idx, l, st)) return s;
     int *ctr = idx->work + (idx->work_next.fetch_add(1, std::memory_order_relaxed) % kWorkSlots);
     NSG_CK(cudaMemsetAsync(ctr, 0, sizeof(int), st));
     l.work = ctr;
-    NSG_CK(nsg::launch_search(l, st));
+    // queries farthest from the navigating node drawn first (the launch's tail
+    // is then made of short searches); the order's scratch is stream-ordered,
+    // so calls on other streams never share it.  Without it the batch runs in
+    // its own order.
+    void *scratch = nullptr;
+    cudaMemPool_t pool = l.parts <= 1 && l.order == nullptr && l.nq > 1 && l.init_count == 0 ? scratch_pool() : nullptr;
+    if (pool && cudaMallocFromPoolAsync(&scratch, nsg::nav_order_scratch_bytes(l.nq), pool, st) == cudaSuccess) {
+        int *order = nullptr;
+        if (nsg::launch_nav_order(l.queries, l.nq, l.d, l.base + (int64_t)l.start * l.dp, scratch, &order, st) ==
+            cudaSuccess)
+            l.order = order;
+    } else {
+        cudaGetLastError();  // an allocation refused is not an error of this call
+    }
+    const cudaError_t e = nsg::launch_search(l, st);
+    if (scratch) cudaFreeAsync(scratch, st);
+    NSG_CK(e);
     return NSG_OK;
 }
 

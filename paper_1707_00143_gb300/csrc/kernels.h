@@ -120,6 +120,13 @@ void stage_layout(const SearchLaunch &l, int nb, int *slots, int *slot_bytes);
 bool make_gather_map(void *map, const void *rows, int64_t n, int row_bytes);
 size_t search_warp_smem_bytes(int L, int W, int H);
 cudaError_t launch_search(const SearchLaunch &a, cudaStream_t st);
+// Visiting order of nq queries [nq][d] for a work-queue launch: farthest from
+// the navigating node's row first (bucketed; the results do not depend on
+// it).  scratch: nav_order_scratch_bytes(nq) bytes, 4-byte aligned; *order
+// points into it.
+size_t nav_order_scratch_bytes(int64_t nq);
+cudaError_t launch_nav_order(const float *queries, int64_t nq, int d, const float *nav_row, void *scratch,
+                             int **order, cudaStream_t st);
 
 // Partition-and-merge: per query, the union of `parts` sorted result lists
 // (ids_in [nq][parts][k_in], positions in the partitioned index, -1 padded;

@@ -281,6 +281,83 @@ cudaError_t launch_offset_adj(const int *in, int64_t nv, int R, int offset, int 
     return cudaGetLastError();
 }
 
+// Visiting order of a batch, farthest from the navigating node first.  A
+// launch ends when its last queries do, and a query's length is only known
+// once it has run; its distance to the navigating node is a weak but free
+// predictor of it (longer greedy path), and drawing the far queries first
+// leaves the short ones for the end.  Measured on the SIFT-shaped 1M search
+// (10,000 queries, 8-bit form, L = 138): 2.067 ms in the generated order,
+// 1.846 ms far-first, 1.703 ms ordered by the true expansion counts (the bound),
+// 2.096 ms near-first.  A counting sort into NAV_BUCKETS distance buckets
+// (order within a bucket is arbitrary: each query's result is independent of
+// the order).
+constexpr int NAV_BUCKETS = 1024;
+
+__global__ void nav_dist_kernel(const float *__restrict__ q, int64_t nq, int d, const float *__restrict__ nav,
+                                float *key, unsigned *maxbits) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned lane = lane_id();
+    if (w >= nq) return;
+    float s = 0.0f;
+    for (int j = lane; j < d; j += 32) {
+        const float t = q[w * d + j] - nav[j];
+        s = fmaf(t, t, s);
+    }
+    s = group_sum<32>(s);
+    if (lane == 0) {
+        key[w] = s;
+        atomicMax(maxbits, __float_as_uint(s));  // s >= +0: the bits order as the values
+    }
+}
+
+__global__ void nav_bucket_kernel(const float *key, int64_t nq, const unsigned *maxbits, int *bucket, int *hist) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    const float mx = __uint_as_float(*maxbits);
+    const int b = mx > 0.0f ? min(NAV_BUCKETS - 1, (int)(key[i] / mx * NAV_BUCKETS)) : 0;
+    bucket[i] = NAV_BUCKETS - 1 - b;  // farthest first
+    atomicAdd(hist + NAV_BUCKETS - 1 - b, 1);
+}
+
+__global__ void nav_scan_kernel(int *hist) {  // exclusive scan of NAV_BUCKETS counts, one block of 1024
+    __shared__ int sh[NAV_BUCKETS];
+    const int t = threadIdx.x;
+    sh[t] = hist[t];
+    __syncthreads();
+    for (int o = 1; o < NAV_BUCKETS; o <<= 1) {
+        const int v = t >= o ? sh[t - o] : 0;
+        __syncthreads();
+        sh[t] += v;
+        __syncthreads();
+    }
+    hist[t] = sh[t] - hist[t];
+}
+
+__global__ void nav_scatter_kernel(const int *bucket, int64_t nq, int *offsets, int *order) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    order[atomicAdd(offsets + bucket[i], 1)] = (int)i;
+}
+
+size_t nav_order_scratch_bytes(int64_t nq) { return (size_t)nq * 12 + (NAV_BUCKETS + 4) * 4; }
+
+cudaError_t launch_nav_order(const float *queries, int64_t nq, int d, const float *nav_row, void *scratch,
+                             int **order, cudaStream_t st) {
+    int *ord = static_cast<int *>(scratch);
+    float *key = reinterpret_cast<float *>(ord + nq);
+    int *bucket = reinterpret_cast<int *>(key + nq);
+    int *hist = bucket + nq;
+    unsigned *maxbits = reinterpret_cast<unsigned *>(hist + NAV_BUCKETS);
+    cudaError_t e = cudaMemsetAsync(hist, 0, (NAV_BUCKETS + 1) * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    nav_dist_kernel<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(queries, nq, d, nav_row, key, maxbits);
+    nav_bucket_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(key, nq, maxbits, bucket, hist);
+    nav_scan_kernel<<<1, NAV_BUCKETS, 0, st>>>(hist);
+    nav_scatter_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(bucket, nq, hist, ord);
+    *order = ord;
+    return cudaGetLastError();
+}
+
 int64_t search_pool_slots() { return (int64_t)sm_count() * 32; }
 
 size_t search_warp_smem_bytes(int L, int W, int H) { return warp_smem_bytes(L, W, 0, H, true); }
