@@ -326,9 +326,10 @@ nsg_status nsg_index_from_graph(const float *base_dev, int64_t n, int32_t d, con
  *   cap -- nsg_search synchronises only in that check.
  *   Warps draw queries from a device counter owned by the index (256 of
  *   them, used in turn): calls on one stream are ordered; at most 256 calls
- *   on one index may be in flight on different streams at once.  They draw
- *   the queries farthest from the navigating node first (a launch ends with
- *   its last searches, and those tend to be the short ones then); each
+ *   on one index may be in flight on different streams at once.  Batches
+ *   larger than the GPU holds at once draw the queries farthest from the
+ *   navigating node first (a launch ends with its last searches, and those
+ *   tend to be the short ones then); each
  *   query's result does not depend on the order.  The order's scratch
  *   (12 bytes per query) comes from a stream-ordered memory pool the library
  *   keeps per device; when it cannot be had the batch runs in its own order.

@@ -1100,11 +1100,15 @@ nsg_status launch_dynamic(const nsg_index *idx, nsg::SearchLaunch l, cudaStream_
     NSG_CK(cudaMemsetAsync(ctr, 0, sizeof(int), st));
     l.work = ctr;
     // queries farthest from the navigating node drawn first (the launch's tail
-    // is then made of short searches); the order's scratch is stream-ordered,
-    // so calls on other streams never share it.  Without it the batch runs in
-    // its own order.
+    // is then made of short searches) when the batch has more warps' worth of
+    // queries than the GPU holds at once (otherwise every query starts at
+    // once); the order's scratch is stream-ordered, so calls on other streams
+    // never share it.  Without it the batch runs in its own order.
     void *scratch = nullptr;
-    cudaMemPool_t pool = l.parts <= 1 && l.order == nullptr && l.nq > 1 && l.init_count == 0 ? scratch_pool() : nullptr;
+    const int64_t resident = (int64_t)nsg::sm_count() * 32;
+    const int wpq = l.warps_per_query > 1 ? l.warps_per_query : 1;
+    const bool order = l.parts <= 1 && l.order == nullptr && l.init_count == 0 && l.nq * wpq > resident;
+    cudaMemPool_t pool = order ? scratch_pool() : nullptr;
     if (pool && cudaMallocFromPoolAsync(&scratch, nsg::nav_order_scratch_bytes(l.nq), pool, st) == cudaSuccess) {
         int *order = nullptr;
         if (nsg::launch_nav_order(l.queries, l.nq, l.d, l.base + (int64_t)l.start * l.dp, scratch, &order, st) ==

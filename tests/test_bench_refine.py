@@ -71,3 +71,35 @@ def test_both_arms_share_the_config():
     base = np.zeros((4, 128), np.float32)
     a, b = bench.bench_config(W, 1, base), bench.bench_config(W, 1, base)
     assert a == b and a["workload"] == W["desc"] and a["target_recall10"] == bench.TARGET
+
+
+def test_config_runs_summarise_children(monkeypatch):
+    # the default line's configuration runs: each child's last JSON line is
+    # summarised; a failing child or one past its time limit is an error entry
+    import json
+    import subprocess
+    import types
+
+    line = {"metric": "m", "value": 2.0, "unit": "queries/s", "config": {"workload": "w"},
+            "operating_point": {"L": 300}, "batched": {"value": 5.0},
+            "at_recall10": {"0.95": {"best": {"u8": {"L": 300, "qps": 2.0, "recall10": 0.95}, "plain": None},
+                                     "stop_vs_fixed_L": {}}}}
+    calls = []
+
+    def fake_run(cmd, capture_output, text, timeout):
+        calls.append((cmd, timeout))
+        wl = cmd[cmd.index("--workload") + 1]
+        assert "--compact" in cmd and "--no-cpu" in cmd
+        if wl == "gist":
+            return types.SimpleNamespace(returncode=0, stdout="noise\n" + json.dumps(line) + "\n", stderr="")
+        raise subprocess.TimeoutExpired(cmd, timeout)
+
+    monkeypatch.setattr(bench.subprocess, "run", fake_run)
+    args = types.SimpleNamespace(steps=7, warmup=3)
+    out = bench.config_runs(args)
+    assert [c[0][c[0].index("--workload") + 1] for c in calls] == [wl for wl, _ in bench.CONFIG_RUNS]
+    g = out["gist"]
+    assert g["value"] == 2.0 and g["batched"] == {"value": 5.0} and g["operating_point"] == {"L": 300}
+    assert g["at_recall10"]["0.95"]["u8"] == {"L": 300, "qps": 2.0} and g["at_recall10"]["0.95"]["plain"] is None
+    assert "--steps 7" in g["command"] and "error" not in g
+    assert out["deep"] == {"error": "no result within %d s" % dict(bench.CONFIG_RUNS)["deep"]}
