@@ -151,7 +151,17 @@ inline int default_hash(int L, int width) {
 // the SIFT-shaped 1M at L = 138 (10,000 queries): 1024 slots re-measure 9 %
 // fewer nodes and run 2-3 % faster than 512 in every form; where 1024 slots
 // cost resident warps (L = 150 and up at R = 50) they are slower.
-inline int default_search_hash(int L, int width) {
+// Visited-set slots of a search when the caller leaves them to the library.
+// A forgotten id is measured again (same key, same results), so a larger set
+// saves distances and costs shared memory: a batch that leaves the SMs short
+// of warps (units search regions, wpq warps each, fewer than 32 warps per SM)
+// takes the largest set up to 4,096 slots whose regions still fit one wave
+// (GIST-shaped 1M, 1,000 queries, 8-bit, 2 warps per query, L = 300: 14,260
+// distances per query and 303 k queries/s with 512 slots, 9,518 and 355 k with
+// 4,096; 8,192 no longer fit one wave: 251 k).  Searches whose rows go
+// through a staging ring, and full batches: 1024 when the search still holds
+// 32 warps per SM with it, else 512.
+inline int default_search_hash(int L, int width, int64_t units = 0, int wpq = 1, bool staged = false) {
     if (L > 1024) return 2048;
     static int smem_sm = 0, reserved = 0;
     if (!smem_sm) {
@@ -161,6 +171,16 @@ inline int default_search_hash(int L, int width) {
         cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
     }
     const int W = (width + 31) & ~31;
+    const int64_t sms = nsg::sm_count();
+    const int64_t regions = (units + sms - 1) / sms;  // per SM, one wave
+    if (!staged && units > 0 && regions * wpq < 32 && smem_sm > 0) {
+        const int rpb = wpq < 4 ? 4 / wpq : 1;  // regions per block of 4 warps
+        const int64_t blocks = (regions + rpb - 1) / rpb;
+        for (int H = 4096; H >= 1024; H >>= 1) {
+            const size_t region = nsg::search_warp_smem_bytes(L, W, H) + 32;
+            if (blocks * (rpb * region + (size_t)reserved) <= (size_t)smem_sm) return H;
+        }
+    }
     const size_t per_block = 4 * nsg::search_warp_smem_bytes(L, W, 1024) + (size_t)reserved;
     return smem_sm > 0 && 8 * per_block <= (size_t)smem_sm ? 1024 : 512;
 }
@@ -1009,7 +1029,7 @@ nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t n
     l.nq = nq;
     l.k = k;
     l.L = L;
-    l.hash_slots = p.hash_slots > 0 ? p.hash_slots : default_search_hash(L, idx->R);
+    l.hash_slots = 0;  // below, once the warps per query are known
     l.max_steps = p.max_steps > 0 ? p.max_steps : nsg::default_steps(L);
     l.warps_per_cta = p.warps_per_cta;
     l.ids = ids_dev;
@@ -1021,6 +1041,9 @@ nsg_status make_search(const nsg_index *idx, const float *queries_dev, int64_t n
     l.init_count = p.init_random;
     l.init_seed = p.init_seed;
     l.warps_per_query = p.warps_per_query > 0 ? p.warps_per_query : nsg::search_auto_wpq(nq, idx->dp, p.precision, L);
+    const bool staged = idx->dp > 512 && (p.stage_rows > 0 || (p.stage_rows == 0 && p.precision == NSG_PREC_F32));
+    l.hash_slots = p.hash_slots > 0 ? p.hash_slots
+                                    : default_search_hash(L, idx->R, nq, l.warps_per_query, staged || p.stop_model);
     if (p.precision != NSG_PREC_F32) {
         l.precision = p.precision;
         l.lowp = idx->lowp[p.precision];
@@ -1473,6 +1496,10 @@ nsg_status nsg_search_trace(const nsg_index *idx, const float *queries_dev, int6
     nsg::SearchLaunch l;
     nsg_status s = make_search(idx, queries_dev, nq, k, L, &p, ids_dev, nullptr, steps_dev, nullptr, nullptr, l);
     if (s || nq == 0) return s;
+    // the traced features count the new neighbours of each expansion, which
+    // the visited set's size changes: traces keep the size the stop model's
+    // searches use (the full-batch rule)
+    if (p.hash_slots <= 0) l.hash_slots = default_search_hash(L, idx->R);
     l.trace_feat = feat_dev;
     l.trace_flag = flag_dev;
     l.trace_cap = cap;
@@ -1571,7 +1598,6 @@ nsg_status nsg_search(const nsg_index *idx, const float *queries_dev, int64_t nq
     l.nq = nq;
     l.k = k;
     l.L = L;
-    l.hash_slots = default_search_hash(L, idx->R);
     l.max_steps = nsg::default_steps(L);
     l.warps_per_cta = 0;
     l.ids = ids_dev;
@@ -1582,6 +1608,7 @@ nsg_status nsg_search(const nsg_index *idx, const float *queries_dev, int64_t nq
     l.any_capped = idx->flag;
     l.stage = -1;  // staged row gathers where they pay (FP32 rows of more than 2 KB)
     l.warps_per_query = nsg::search_auto_wpq(nq, idx->dp, NSG_PREC_F32, L);
+    l.hash_slots = default_search_hash(L, idx->R, nq, l.warps_per_query, idx->dp > 512);
     l.pool_global = L > 1024;
     NSG_CK(cudaMemsetAsync(idx->flag, 0, sizeof(int), st));
     if (nsg_status ls = launch_dynamic(idx, l, st)) return ls;
