@@ -1130,13 +1130,13 @@ nsg_status launch_dynamic(const nsg_index *idx, nsg::SearchLaunch l, cudaStream_
     void *scratch = nullptr;
     const int64_t resident = (int64_t)nsg::sm_count() * 32;
     const int wpq = l.warps_per_query > 1 ? l.warps_per_query : 1;
-    const bool order = l.parts <= 1 && l.order == nullptr && l.init_count == 0 && l.nq * wpq > resident;
-    cudaMemPool_t pool = order ? scratch_pool() : nullptr;
+    const bool ordered = l.parts <= 1 && l.order == nullptr && l.init_count == 0 && l.nq * wpq > resident;
+    cudaMemPool_t pool = ordered ? scratch_pool() : nullptr;
     if (pool && cudaMallocFromPoolAsync(&scratch, nsg::nav_order_scratch_bytes(l.nq), pool, st) == cudaSuccess) {
-        int *order = nullptr;
-        if (nsg::launch_nav_order(l.queries, l.nq, l.d, l.base + (int64_t)l.start * l.dp, scratch, &order, st) ==
+        int *ord = nullptr;
+        if (nsg::launch_nav_order(l.queries, l.nq, l.d, l.base + (int64_t)l.start * l.dp, scratch, &ord, st) ==
             cudaSuccess)
-            l.order = order;
+            l.order = ord;
     } else {
         cudaGetLastError();  // an allocation refused is not an error of this call
     }
