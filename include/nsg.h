@@ -57,11 +57,11 @@ typedef struct {
     int32_t max_steps;     /* expansion cap per query; <= 0 -> 16*L + 4096 */
     int32_t hash_slots;    /* visited-hash slots per query (power of 2, 64..65536); <= 0 -> auto:
                               a batch that leaves the SMs short of warps (and stages no rows,
-                              has no stop model) takes the largest set up to 4096 whose query
-                              regions still fit one wave; otherwise 1024 when the search still
-                              holds 32 warps per SM with it (small pools), else 512; 2048 above
-                              L = 1024.  The same results at any size (a forgotten node is
-                              measured again) */
+                              has no stop model) takes the largest set up to 4096 (8192 above
+                              L = 1024) whose query regions still fit one wave; otherwise 1024
+                              when the search still holds 32 warps per SM with it (small
+                              pools), else 512; 2048 above L = 1024.  The same results at any
+                              size (a forgotten node is measured again) */
     int32_t precision;     /* nsg_precision of the traversal distances */
     int32_t warps_per_cta; /* <= 0 -> auto */
     int32_t rerank;        /* BF16/FP8/U8: re-rank the final pool with FP32 rows (1), not (0),

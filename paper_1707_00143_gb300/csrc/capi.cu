@@ -158,11 +158,11 @@ inline int default_hash(int L, int width) {
 // takes the largest set up to 4,096 slots whose regions still fit one wave
 // (GIST-shaped 1M, 1,000 queries, 8-bit, 2 warps per query, L = 300: 14,260
 // distances per query and 303 k queries/s with 512 slots, 9,518 and 355 k with
-// 4,096; 8,192 no longer fit one wave: 251 k).  Searches whose rows go
-// through a staging ring, and full batches: 1024 when the search still holds
-// 32 warps per SM with it, else 512.
+// 4,096; 8,192 no longer fit one wave: 251 k); pools above 1024 keys (in
+// global memory) up to 8,192 slots.  Searches whose rows go through a staging
+// ring, and full batches: 2048 above L = 1024, else 1024 when the search
+// still holds 32 warps per SM with it, else 512.
 inline int default_search_hash(int L, int width, int64_t units = 0, int wpq = 1, bool staged = false) {
-    if (L > 1024) return 2048;
     static int smem_sm = 0, reserved = 0;
     if (!smem_sm) {
         int dev = 0;
@@ -173,14 +173,16 @@ inline int default_search_hash(int L, int width, int64_t units = 0, int wpq = 1,
     const int W = (width + 31) & ~31;
     const int64_t sms = nsg::sm_count();
     const int64_t regions = (units + sms - 1) / sms;  // per SM, one wave
+    const int Ls = L > 1024 ? 0 : L;                  // pools above 1024 keys live in global memory
     if (!staged && units > 0 && regions * wpq < 32 && smem_sm > 0) {
         const int rpb = wpq < 4 ? 4 / wpq : 1;  // regions per block of 4 warps
         const int64_t blocks = (regions + rpb - 1) / rpb;
-        for (int H = 4096; H >= 1024; H >>= 1) {
-            const size_t region = nsg::search_warp_smem_bytes(L, W, H) + 32;
+        for (int H = L > 1024 ? 8192 : 4096; H >= (L > 1024 ? 2048 : 1024); H >>= 1) {
+            const size_t region = nsg::search_warp_smem_bytes(Ls, W, H) + 32;
             if (blocks * (rpb * region + (size_t)reserved) <= (size_t)smem_sm) return H;
         }
     }
+    if (L > 1024) return 2048;
     const size_t per_block = 4 * nsg::search_warp_smem_bytes(L, W, 1024) + (size_t)reserved;
     return smem_sm > 0 && 8 * per_block <= (size_t)smem_sm ? 1024 : 512;
 }
