@@ -103,3 +103,24 @@ def test_config_runs_summarise_children(monkeypatch):
     assert g["at_recall10"]["0.95"]["u8"] == {"L": 300, "qps": 2.0} and g["at_recall10"]["0.95"]["plain"] is None
     assert "--steps 7" in g["command"] and "error" not in g
     assert out["deep"] == {"error": "no result within %d s" % dict(bench.CONFIG_RUNS)["deep"]}
+
+
+def test_build_index_follows_the_workloads_knn_stage():
+    # the DEEP-shaped workload builds on an nn-descent kNN stage, the others on
+    # the exact one; the line's config names which
+    import types
+
+    calls = []
+    fake = types.SimpleNamespace(
+        nsg_build=lambda bt, K, L, R, C, seed=0: calls.append(("exact", K, L, R, C, seed)) or "idx",
+        nsg_build_ex=lambda bt, K, L, R, C, seed=0, knn_params=None: calls.append(
+            ("nndescent", K, L, R, C, seed, knn_params)) or "idx",
+        NnDescentParams=lambda *a: tuple(a))
+    assert bench.build_index(fake, None, bench.WORKLOADS["sift"]) == "idx"
+    assert bench.build_index(fake, None, bench.WORKLOADS["deep"], seed=3) == "idx"
+    assert calls[0] == ("exact", 100, 40, 50, 500, 0)
+    assert calls[1][:6] == ("nndescent", 64, 60, 32, 500, 3) and calls[1][6][:3] == bench.WORKLOADS["deep"]["knn"]
+    import numpy as np
+    base = np.zeros((4, 2), np.float32)
+    assert "nn-descent" in bench.bench_config(bench.WORKLOADS["deep"], 1, base)["knn_stage"]
+    assert bench.bench_config(bench.WORKLOADS["sift"], 1, base)["knn_stage"].startswith("exact")
