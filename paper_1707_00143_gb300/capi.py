@@ -31,6 +31,12 @@ class NsgError(RuntimeError):
 
 
 class SearchParams(C.Structure):
+    """nsg_search_params (include/nsg.h has each field's full meaning).  Zero
+    leaves a choice to the library: max_steps (16 L + 4096), hash_slots (sized
+    to the batch), warps_per_cta, warps_per_query and stage_rows (measured
+    rules), pool (shared memory up to L = 1024); rerank -1 re-ranks only lossy
+    copies.  stop_model: a device tensor of NSG_STOP_PARAMS FP16 values or None.
+    No choice changes a query's result."""
     _fields_ = [("max_steps", C.c_int32), ("hash_slots", C.c_int32), ("precision", C.c_int32),
                 ("warps_per_cta", C.c_int32), ("rerank", C.c_int32), ("stop_model", C.c_void_p),
                 ("stop_threshold", C.c_float), ("stop_k", C.c_int32), ("stop_min_steps", C.c_int32),
