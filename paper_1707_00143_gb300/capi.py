@@ -36,7 +36,8 @@ class SearchParams(C.Structure):
     to the batch), warps_per_cta, warps_per_query and stage_rows (measured
     rules), pool (shared memory up to L = 1024); rerank -1 re-ranks only lossy
     copies.  stop_model: a device tensor of NSG_STOP_PARAMS FP16 values or None.
-    No choice changes a query's result."""
+    None of those automatic choices (hash_slots, warps_per_cta, warps_per_query,
+    stage_rows, pool) changes a query's result."""
     _fields_ = [("max_steps", C.c_int32), ("hash_slots", C.c_int32), ("precision", C.c_int32),
                 ("warps_per_cta", C.c_int32), ("rerank", C.c_int32), ("stop_model", C.c_void_p),
                 ("stop_threshold", C.c_float), ("stop_k", C.c_int32), ("stop_min_steps", C.c_int32),
