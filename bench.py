@@ -895,6 +895,8 @@ def main():
     tr = NCU_TRAFFIC.get((src, args.workload, chosen_form, L))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": (tr * nq if tr else None),
+                # the captured DRAM traffic over the same time: what HBM actually moved
+                "dram_gbs": (tr * nq / (ms_step / 1e3) / 1e9 if tr else None),
                 "peak_kind": peak_kind, "kernel": f"search_kernel ({chosen_form})",
                 "algorithmic_bytes": bytes_launch, "kernel_src": src}
     # instruction issue: the search kernel is bound by it (ncu: ~73 % of active cycles
