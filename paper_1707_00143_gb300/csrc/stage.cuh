@@ -8,7 +8,9 @@
 // and sums as the register gather, so the same keys) and refills the slot
 // with row c + nb.  Rows past the ring are prefetched into L2 first, so the
 // refills come from L2.  The keys are the register gather's, so the search's
-// steps and results are too.
+// steps and results are too.  Rows with a tensor map over them (the BF16 /
+// FP8 / U8 copies of rows of at most 2 KB) are gathered four per copy
+// instead: a slot holds the four rows of one tile::gather4.
 //
 // Measured (GIST-shaped 1M x 960, k = 100, L = 300, one query alone): a
 // staged row costs ~0.4 us whether it is 960 or 3,840 bytes and whatever the
@@ -17,8 +19,10 @@
 // takes 17.8 us staged against 7.1 us in registers (8 rows in flight per
 // lane group), while FP32 rows, two in flight per group in registers, take
 // the same 20.4 us either way; in a batch the staged FP32 form with 4 slots
-// frees the registers the gather held and runs 7-38 % faster.  The launch
-// therefore stages only FP32-sized rows (more than 2 KB) by default.
+// frees the registers the gather held and runs 7-38 % faster.  Four-row
+// gathers take the 8-bit expansion to 13.4 us: the rows of one gather also
+// arrive one after another.  The launch therefore stages only FP32-sized
+// rows (more than 2 KB) by default.
 //
 // Every wait is bounded (STAGE_TIMEOUT_NS).  A copy that never lands marks
 // the warp failed: it drains (again bounded) the copies it still has in
